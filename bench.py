@@ -1,0 +1,306 @@
+"""Throughput benchmark of the FFT/tridiagonal Poisson solve (one JSON line on rank 0).
+
+Default workload (N=1): a 1024^3 cell-centred grid, Neumann x / Dirichlet y / Neumann z,
+f i.i.d. U[-1,1] (seeded) with the mean removed, FP64 in/out.  One step = one full solve
+(x-forward, y-forward, z tridiagonal, y-inverse, x-inverse), timed with CUDA events on the
+launching stream; inputs (8 GiB) exceed the 129 MB L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--n 1024] [--impl ours|reference]
+
+--impl reference times the CPU oracle (naive O(N^2) transforms + Thomas, OpenMP on the host
+cores) on a bounded slab of the same workload.  Under torchrun (N>1) every rank solves its own
+grid (independent replicas, no collective on the data path); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gpoints/s per Poisson solve at 1024^3, FP64 vs mixed; % of HBM roofline"
+UNIT = "Gpoints/s"
+BC = "NNDDNN"
+SEED = 2
+STAGES = ["x-forward", "y-forward", "z-solve", "y-inverse", "x-inverse"]
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    return rank, world
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _oracle_sample(n: int, nz_sample: int, seed: int):
+    """Time the CPU oracle on an n x n x nz_sample slab of the workload; returns (seconds, points, threads).
+    The per-point cost of the oracle's x/y transforms depends only on n, so the slab's rate is the
+    rate of the full n^3 workload (the z part is O(nz) per mode in both)."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    f = np.random.default_rng(seed).uniform(-1.0, 1.0, size=(nz_sample, n, n))
+    t0 = time.perf_counter()
+    oracle.solve(f, BC, (1.0 / n, 1.0 / n, 1.0 / n))
+    dt = time.perf_counter() - t0
+    return dt, f.size, oracle.num_threads()
+
+
+def run_reference(args):
+    rank, world = _dist()
+    if rank != 0:
+        return 0
+    n = args.n
+    nzs = args.oracle_planes
+    for _ in range(args.warmup):
+        _oracle_sample(n, max(1, nzs // 4), SEED)
+    times, pts, threads = [], 0, 1
+    for _ in range(args.steps):
+        dt, pts, threads = _oracle_sample(n, nzs, SEED)
+        times.append(dt)
+    tot = sum(times)
+    value = pts * len(times) / tot / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded U[-1,1])",
+        "config": {"workload": "%d^3 FP64 Neumann-x/Dirichlet-y/Neumann-z, U[-1,1] source" % n,
+                   "bc": BC, "n": n, "sample": "%dx%dx%d slab per step" % (n, n, nzs)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "oracle solve of a %dx%dx%d slab per step (naive O(N^2) transforms)" % (n, n, nzs)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1909_05423_gb300 as pp
+    from paper_1909_05423_gb300 import _lib, workloads
+
+    rank, world = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    n = args.n
+    shape = (n, n, n)
+    sp = (1.0 / n,) * 3
+    npts = n ** 3
+    lib = _lib.load()
+
+    # input: seeded U[-1,1], mean removed, generated on the device
+    g = torch.Generator(device="cuda")
+    g.manual_seed(SEED + rank)
+    f = torch.empty(shape, dtype=torch.float64, device="cuda").uniform_(-1.0, 1.0, generator=g)
+    f -= f.mean()
+    u = torch.empty_like(f)
+    stream = torch.cuda.current_stream()
+    sh = _lib.ctypes.c_void_p(stream.cuda_stream)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(plan, fin, uout, steps, warmup):
+        """Run warmup + steps solves stage by stage with events between stages.
+        Returns (ms per step, per-stage mean ms)."""
+        h = plan.handle
+        fp, up = _lib.ctypes.c_void_p(fin.data_ptr()), _lib.ctypes.c_void_p(uout.data_ptr())
+        for _ in range(warmup):
+            _lib.check(lib.pp_solve(h, fp, up, sh))
+        barrier()
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(steps)]
+        for s in range(steps):
+            ev[s][0].record(stream)
+            for st in range(5):
+                _lib.check(lib.pp_run_stage(h, st, fp, up, sh))
+                ev[s][st + 1].record(stream)
+        barrier()
+        tot = sum(ev[s][0].elapsed_time(ev[s][5]) for s in range(steps))
+        per = [sum(ev[s][k].elapsed_time(ev[s][k + 1]) for s in range(steps)) / steps for k in range(5)]
+        return tot / steps, per
+
+    # ---------------------------------------------------------------- FP64 path (headline)
+    plan = pp.Plan(shape, BC, sp, "f64")
+    clocks = Clocks(local)
+    barrier()
+    clocks.start()
+    ms, per = timed(plan, f, u, args.steps, args.warmup)
+    clk = clocks.stop()
+    ms_all = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_all = t.item()
+    plan.status()
+    value = world * npts / (ms_all * 1e-3) / 1e9
+
+    # roofline of the dominant kernel: algorithmic bytes = read input once + write output once
+    elem = 8  # FP64 I/O and double-float spill: 8 bytes per real
+    xs = (n + 2) / n if BC[0] == "P" else 1.0
+    alg_bytes = {"x-forward": npts * elem * (1 + xs), "y-forward": 2 * npts * elem * xs,
+                 "z-solve": 2 * npts * elem * xs, "y-inverse": 2 * npts * elem * xs,
+                 "x-inverse": npts * elem * (1 + xs)}
+    dom = max(range(5), key=lambda k: per[k])
+    dname = STAGES[dom]
+    peak, peak_kind = _peaks()
+    achieved = alg_bytes[dname] / (per[dom] * 1e-3) / 1e9
+    path_gbs = 32.0 * npts / (ms * 1e-3) / 1e9
+
+    # ---------------------------------------------------------------- mixed precision variants
+    variants = {}
+    if not args.no_mixed:
+        pm = pp.Plan(shape, BC, sp, "mixed_f64io")
+        um = torch.empty_like(f)
+        ms_m, per_m = timed(pm, f, um, args.steps, args.warmup)
+        torch.cuda.synchronize()
+        err_m = (torch.linalg.vector_norm(um - u) / torch.linalg.vector_norm(u)).item()
+        variants["mixed_f64io"] = {"value": npts / (ms_m * 1e-3) / 1e9, "ms_per_step": ms_m,
+                                   "stage_ms": dict(zip(STAGES, per_m)), "speedup_vs_f64": ms / ms_m,
+                                   "rel_l2_vs_f64_path": err_m}
+        pm.close()
+        del um
+
+    # ---------------------------------------------------------------- end to end through host buffers
+    e2e = None
+    if not args.no_e2e:
+        fh = torch.empty(shape, dtype=torch.float64, pin_memory=True)
+        fh.copy_(f.cpu())
+        uh = torch.empty(shape, dtype=torch.float64, pin_memory=True)
+        plan.solve_host(fh, uh)
+        barrier()
+        t0 = time.perf_counter()
+        ke = max(1, min(args.steps, 3))
+        for _ in range(ke):
+            plan.solve_host(fh, uh)
+        dt = (time.perf_counter() - t0) / ke
+        e2e = {"value": npts / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": npts * 8, "d2h_bytes_per_step": npts * 8}
+        del fh, uh
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        dt, pts, threads = _oracle_sample(n, args.oracle_planes, SEED)
+        cpu = {"value": pts / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "oracle solve of a %dx%dx%d slab of the same workload (naive O(N^2) transforms, "
+                         "per-point cost independent of nz)" % (n, n, args.oracle_planes)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 I/O, double-float (2xf32) transforms and z-solve",
+            "data": "synthetic (seeded U[-1,1], mean removed; generated on device)",
+            "config": {"workload": "%d^3 FP64 Neumann-x/Dirichlet-y/Neumann-z, U[-1,1] source" % n, "bc": BC,
+                       "n": n, "points": npts, "l2": "inputs (8 GiB/grid) exceed L2; no flush",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "stage_ms": dict(zip(STAGES, per)), "path_hbm_gbs_32B_per_point": path_gbs,
+                       "path_hbm_frac_32B_per_point": path_gbs / peak},
+            "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                         "alg_bytes_per_launch": alg_bytes[dname]},
+            "variants": variants,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": 5 * args.steps,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--oracle-planes", type=int, default=8)
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,156 @@
+/*
+ * pittpack_gb.h -- C ABI of the GB300 FFT/tridiagonal Poisson solver.
+ *
+ * The library solves the second-order, cell-centred 7-point discretisation of
+ * Poisson's equation (Hasbestan & Senocak, arXiv 1909.05423, Sec. "Mathematical
+ * Formulation"):
+ *
+ *   (u[i+1]-2u[i]+u[i-1])/dx^2 + (same in y)/dy^2 + (same in z)/dz^2 = f
+ *
+ * on an nx x ny x nz grid of cells, by the paper's direct method: forward line
+ * transforms in x and y chosen per boundary condition (Sec. "Boundary
+ * Conditions", table of forward/backward transforms), one tridiagonal system
+ * along z per (kx,ky) pair with the diagonal shifted by the eigenvalues of
+ * Table "Eigenvalues" (Sec. "Solution of the Resulting Tridiagonal Matrices";
+ * Thomas algorithm, Sherman-Morrison for periodic z), and the inverse
+ * transforms.  Everything runs on one GPU, on caller-owned device memory.
+ *
+ * Conventions
+ *  - Grids are real arrays [nz][ny][nx], x fastest (C order), cell centres at
+ *    ((i+1/2)dx, (j+1/2)dy, (k+1/2)dz).
+ *  - Faces are ordered x-, x+, y-, y+, z-, z+.  Boundary conditions are
+ *    homogeneous: periodic (must be given on both faces of an axis), Neumann
+ *    (ghost u[-1] = u[0]) or Dirichlet with zero face value by linear
+ *    extrapolation (ghost u[-1] = -u[0], Sec. "Dirichlet-type Boundary
+ *    Condition").  Non-zero face values are folded into f by the caller.
+ *  - With no Dirichlet face the operator is singular (Sec. "Well-posedness");
+ *    the library then returns the zero-mean u with A u = f - mean(f).
+ *  - Sizes: nx and ny must be even and of the form 2^a 3^b (a >= 1),
+ *    2 <= nx, ny <= 4096; nz >= 2 (periodic z: nz >= 3).  Anything else
+ *    returns PP_ERR_UNSUPPORTED_SIZE.
+ *  - All solve calls are asynchronous on the given CUDA stream (NULL = legacy
+ *    default stream).  The returned status reports argument validation and
+ *    launch errors; device-side errors are reported by pp_plan_status() after
+ *    the stream has been synchronised.
+ *  - Error detail for the calling thread: pp_last_error_string().
+ *  - A plan may be used by one stream at a time (its workspace is shared by
+ *    all of its calls).
+ */
+#ifndef PITTPACK_GB_H
+#define PITTPACK_GB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* pp_stream_t; /* identical to cudaStream_t */
+
+typedef enum { PP_BC_PERIODIC = 0, PP_BC_NEUMANN = 1, PP_BC_DIRICHLET = 2 } pp_bc;
+
+typedef enum {
+  PP_F64 = 0,         /* FP64 in/out; FP64-class (double-float, ~47-bit) transforms and z-solve */
+  PP_MIXED_F64IO = 1, /* FP64 in/out; FP32 transforms; z-solve in double-float arithmetic */
+  PP_MIXED_F32IO = 2  /* FP32 in/out; FP32 transforms; z-solve in double-float arithmetic */
+} pp_dtype;
+
+typedef enum {
+  PP_OK = 0,
+  PP_ERR_INVALID_ARG = 1,
+  PP_ERR_UNSUPPORTED_SIZE = 2,
+  PP_ERR_BC_PAIRING = 3,
+  PP_ERR_OUT_OF_MEMORY = 4,
+  PP_ERR_CUDA = 5,
+  PP_ERR_TIMEOUT = 6,
+  PP_ERR_INTERNAL = 7
+} pp_status;
+
+/* Optional plan settings; pass NULL for the defaults. */
+typedef struct pp_plan_options {
+  int threads_x;   /* CTA size of the x-line kernels (0 = automatic) */
+  int threads_y;   /* CTA size of the y-line kernels (0 = automatic) */
+  int lines_x;     /* lines per CTA, x kernels (0 = automatic) */
+  int cols_y;      /* columns per CTA, y kernels (0 = automatic) */
+  int reserved[8]; /* must be zero */
+} pp_plan_options;
+
+typedef struct pp_plan pp_plan;
+
+/* Create a plan (Sec. "Mathematical Formulation"; user API of the paper's appendix:
+ * grid size, per-face boundary conditions, spacings).
+ *   out       : receives the plan handle (owned by the caller; free with pp_plan_destroy)
+ *   nx,ny,nz  : cells per axis (see size rules above)
+ *   bc        : 6 face conditions, order x-,x+,y-,y+,z-,z+
+ *   dx,dy,dz  : cell sizes (> 0)
+ *   dtype     : arithmetic / I/O mode
+ *   opt       : NULL or launch-shape overrides
+ * Allocates the plan's device workspace (two spectral buffers) and its coefficient
+ * tables on the current device.  Errors: PP_ERR_INVALID_ARG, PP_ERR_UNSUPPORTED_SIZE,
+ * PP_ERR_BC_PAIRING, PP_ERR_OUT_OF_MEMORY, PP_ERR_CUDA; *out is NULL on error. */
+pp_status pp_plan_create(pp_plan** out, int nx, int ny, int nz, const pp_bc bc[6], double dx, double dy,
+                         double dz, pp_dtype dtype, const pp_plan_options* opt);
+
+/* Solve A u = f (Secs. "Boundary Conditions" to "Solution of the Resulting Tridiagonal
+ * Matrices").  f_dev, u_dev: device arrays of nx*ny*nz doubles (PP_F64, PP_MIXED_F64IO)
+ * or floats (PP_MIXED_F32IO), owned by the caller; u may alias f.  Asynchronous on
+ * stream.  Errors: PP_ERR_INVALID_ARG (NULL plan/pointer), PP_ERR_CUDA (launch). */
+pp_status pp_solve(pp_plan* plan, const void* f_dev, void* u_dev, pp_stream_t stream);
+
+/* Mixed precision with one FP64 residual-refinement step: u0 = solve(f),
+ * r = f - A u0 (7-point stencil of Sec. "Mathematical Formulation", evaluated in
+ * double-float arithmetic), u = u0 + solve(r).  Only for PP_MIXED_F64IO plans
+ * (PP_ERR_INVALID_ARG otherwise).  u must not alias f. */
+pp_status pp_solve_refined(pp_plan* plan, const void* f_dev, void* u_dev, pp_stream_t stream);
+
+/* Solve n independent problems, plans[i] applied to (f[i] -> u[i]), enqueued back to
+ * back on one stream (each plan owns its workspace, so the solves do not interfere).
+ * Errors as pp_solve; the first failing index stops the enqueueing. */
+pp_status pp_solve_batched(pp_plan* const* plans, const void* const* f, void* const* u, int n,
+                           pp_stream_t stream);
+
+/* Adjoint: g_f = S^T g, where S is the solution operator f -> u.  Runs the transposed
+ * pipeline (transposed inverse transforms, transposed tridiagonal factorisation,
+ * transposed forward transforms).  Because A is symmetric for periodic, Neumann and
+ * Dirichlet faces, S^T = S; the explicit transposed pipeline is what is executed.
+ * Same argument rules as pp_solve. */
+pp_status pp_solve_adjoint(pp_plan* plan, const void* g_dev, void* gf_dev, pp_stream_t stream);
+
+/* pp_solve on HOST buffers: copies f to the device, solves, copies u back, all on
+ * stream, and synchronises the stream before returning.  Device staging buffers are
+ * allocated by the first call on a plan.  f_host, u_host: nx*ny*nz elements of the
+ * plan's I/O type (pinned memory gives full copy bandwidth). */
+pp_status pp_solve_host(pp_plan* plan, const void* f_host, void* u_host, pp_stream_t stream);
+
+/* Run one stage of the pp_solve pipeline on its own (for per-kernel timing and profiling):
+ *   stage 0: x-forward transform   f -> plan workspace A
+ *   stage 1: y-forward transform   A -> B
+ *   stage 2: z tridiagonal solves  B in place
+ *   stage 3: y-inverse transform   B -> A
+ *   stage 4: x-inverse transform   A -> u
+ * Running stages 0..4 in order on one stream is exactly pp_solve(plan, f, u, stream).
+ * f is read only by stage 0 and u written only by stage 4 (either may be NULL otherwise).
+ * Errors: PP_ERR_INVALID_ARG (bad stage / NULL pointer), PP_ERR_CUDA (launch). */
+pp_status pp_run_stage(pp_plan* plan, int stage, const void* f_dev, void* u_dev, pp_stream_t stream);
+
+/* Release the plan and its device memory (synchronises the device first). NULL is a no-op. */
+pp_status pp_plan_destroy(pp_plan* plan);
+
+/* Device-side status of the plan's last solves (PP_OK unless a kernel reported an error).
+ * Call after synchronising the stream; reading clears it. */
+pp_status pp_plan_status(pp_plan* plan);
+
+/* Bytes of device memory held by the plan (workspace + tables). */
+size_t pp_plan_device_bytes(const pp_plan* plan);
+
+/* Human-readable detail of the last error on the calling thread ("" if none). */
+const char* pp_last_error_string(void);
+
+/* Library version string. */
+const char* pp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PITTPACK_GB_H */

@@ -1,0 +1,246 @@
+// pp_arith.cuh -- arithmetic types of the GPU path.
+//
+// GB300 runs FP64 at about 1/67 of its FP32 rate, and FP32<->FP64 conversion
+// instructions at the FP64 rate.  The FP64-accurate path therefore computes in
+// "double-float" arithmetic: a value is an unevaluated sum hi + lo of two FP32
+// numbers (Dekker 1971, "A floating-point technique for extending the available
+// precision"; Knuth's TwoSum), giving a ~47-bit significand.  FP64 grid values
+// are split into (hi, lo) and re-assembled with integer bit operations, which
+// run at full rate.  The mixed-precision path uses plain FP32 for the
+// transforms and the same double-float arithmetic in the tridiagonal solve.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pp {
+
+// ---------------------------------------------------------------- double-float
+struct __align__(8) df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df df_make(float h) { return df{h, 0.0f}; }
+
+// Knuth TwoSum: s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// Dekker FastTwoSum (|a| >= |b|): s + e == a + b exactly.
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ df operator+(df a, df b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  df r;
+  fast_two_sum(s, e, r.hi, r.lo);
+  return r;
+}
+__device__ __forceinline__ df operator-(df a) { return df{-a.hi, -a.lo}; }
+__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+// product with FMA-based TwoProd; the lo*lo term (2^-48 relative) is dropped.
+__device__ __forceinline__ df operator*(df a, df b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  df r;
+  fast_two_sum(p, e, r.hi, r.lo);
+  return r;
+}
+// a*b - c*d with one renormalisation (used by the complex product).
+__device__ __forceinline__ df dot2_sub(df a, df b, df c, df d) {
+  float p1 = __fmul_rn(a.hi, b.hi);
+  float e1 = __fmaf_rn(a.hi, b.hi, -p1);
+  float p2 = __fmul_rn(c.hi, d.hi);
+  float e2 = __fmaf_rn(c.hi, d.hi, -p2);
+  float s, e;
+  two_sum(p1, -p2, s, e);
+  e = __fadd_rn(e, __fsub_rn(e1, e2));
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  e = __fmaf_rn(-c.hi, d.lo, e);
+  e = __fmaf_rn(-c.lo, d.hi, e);
+  df r;
+  fast_two_sum(s, e, r.hi, r.lo);
+  return r;
+}
+// a*b + c*d
+__device__ __forceinline__ df dot2_add(df a, df b, df c, df d) { return dot2_sub(a, b, -c, d); }
+__device__ __forceinline__ df df_half(df a) { return df{0.5f * a.hi, 0.5f * a.lo}; }
+
+// df reciprocal: one Newton step on the FP32 reciprocal.
+__device__ __forceinline__ df df_rcp(df a) {
+  float r = __frcp_rn(a.hi);
+  df one = df{1.0f, 0.0f};
+  df ra = df{r, 0.0f};
+  df err = one - a * ra;     // 1 - a r
+  return ra + ra * err;      // r (1 + (1 - a r))
+}
+
+// ------------------------------------------------ FP64 <-> double-float (integer)
+// Split an FP64 value into hi + lo (hi = truncated 24-bit significand, lo = the next 23 bits),
+// using integer operations only.  |d| < 2^-103 keeps only hi; |d| < 2^-126 flushes to zero.
+__device__ __forceinline__ df df_from_double(double d) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
+  unsigned sign = h32 & 0x80000000u;
+  int e = (int)((h32 >> 20) & 0x7ffu);
+  int ef = e - 896;  // float biased exponent
+  unsigned mh = ((h32 & 0xfffffu) << 3) | (l32 >> 29);
+  df r;
+  if (ef >= 255) {  // overflow / inf / nan
+    r.hi = __uint_as_float(sign | 0x7f800000u | (e == 0x7ff && ((h32 & 0xfffffu) | l32) ? 0x400000u : 0u));
+    r.lo = 0.0f;
+    return r;
+  }
+  if (ef < 1) { r.hi = __uint_as_float(sign); r.lo = 0.0f; return r; }
+  r.hi = __uint_as_float(sign | ((unsigned)ef << 23) | mh);
+  if (ef >= 24) {
+    unsigned base = sign | ((unsigned)(ef - 23) << 23);
+    r.lo = __fsub_rn(__uint_as_float(base | ((l32 & 0x1fffffffu) >> 6)), __uint_as_float(base));
+  } else {
+    r.lo = 0.0f;
+  }
+  return r;
+}
+
+// Assemble hi + lo into the FP64 value (truncated to 53 bits), integer operations only.
+__device__ __forceinline__ double df_to_double(df v) {
+  unsigned hb = __float_as_uint(v.hi), lb = __float_as_uint(v.lo);
+  int eh = (int)((hb >> 23) & 0xffu);
+  unsigned long long sign = (unsigned long long)(hb & 0x80000000u) << 32;
+  if (eh == 0) return __longlong_as_double((long long)sign);
+  if (eh == 255) return __longlong_as_double((long long)(sign | 0x7ff0000000000000ull |
+                                                          ((hb & 0x7fffffu) ? 0x8000000000000ull : 0ull)));
+  long long X = (long long)(((unsigned long long)((hb & 0x7fffffu) | 0x800000u)) << 29);
+  int el = (int)((lb >> 23) & 0xffu);
+  if (el != 0) {
+    long long Ml = (long long)((lb & 0x7fffffu) | 0x800000u);
+    int sh = (eh - el) - 29;  // right shift of lo's 24-bit significand into units of 2^(eh-127-52)
+    long long L = (sh <= 0) ? (Ml << (-sh < 40 ? -sh : 40)) : (sh < 40 ? (Ml >> sh) : 0);
+    X = ((hb ^ lb) & 0x80000000u) ? X - L : X + L;
+  }
+  int e = eh - 127 + 1023;
+  if (X >= (1LL << 53)) { X >>= 1; e += 1; }
+  else if (X < (1LL << 52)) { X <<= 1; e -= 1; }
+  unsigned long long bits = sign | ((unsigned long long)e << 52) | ((unsigned long long)X & 0xfffffffffffffull);
+  return __longlong_as_double((long long)bits);
+}
+
+// FP64 -> FP32 rounded to nearest (ties away), integer operations only.
+__device__ __forceinline__ float f32_from_double(double d) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
+  unsigned sign = h32 & 0x80000000u;
+  int e = (int)((h32 >> 20) & 0x7ffu);
+  int ef = e - 896;
+  if (ef >= 255) return __uint_as_float(sign | 0x7f800000u | (e == 0x7ff && ((h32 & 0xfffffu) | l32) ? 0x400000u : 0u));
+  if (ef < 1) return __uint_as_float(sign);
+  unsigned mag = ((unsigned)ef << 23) | ((h32 & 0xfffffu) << 3) | (l32 >> 29);
+  mag += (l32 >> 28) & 1u;  // round half away from zero; a carry into the exponent is correct
+  if (mag >= 0x7f800000u) mag = 0x7f800000u;
+  return __uint_as_float(sign | mag);
+}
+
+// FP32 -> FP64, exact, integer operations only (denormal floats flush to zero).
+__device__ __forceinline__ double double_from_f32(float f) {
+  unsigned u = __float_as_uint(f);
+  unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  unsigned ef = (u >> 23) & 0xffu;
+  if (ef == 0) return __longlong_as_double((long long)sign);
+  if (ef == 255) return __longlong_as_double((long long)(sign | 0x7ff0000000000000ull |
+                                                          ((u & 0x7fffffu) ? 0x8000000000000ull : 0ull)));
+  unsigned long long bits = sign | ((unsigned long long)(ef + 896) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
+__device__ __forceinline__ float df_to_f32(df v) { return __fadd_rn(v.hi, v.lo); }
+
+// ------------------------------------------------------------- scalar traits
+template <class R> struct Ar;
+template <> struct Ar<float> {
+  __device__ static __forceinline__ float add(float a, float b) { return a + b; }
+  __device__ static __forceinline__ float sub(float a, float b) { return a - b; }
+  __device__ static __forceinline__ float mul(float a, float b) { return a * b; }
+  __device__ static __forceinline__ float neg(float a) { return -a; }
+  __device__ static __forceinline__ float half(float a) { return 0.5f * a; }
+  __device__ static __forceinline__ float zero() { return 0.0f; }
+  __device__ static __forceinline__ float sqrt1_2() { return 0.70710678118654752f; }
+  __device__ static __forceinline__ float sqrt3_2() { return 0.86602540378443865f; }
+  __device__ static __forceinline__ float sqrt2() { return 1.41421356237309505f; }
+  // complex product parts: a*b - c*d and a*b + c*d
+  __device__ static __forceinline__ float dsub(float a, float b, float c, float d) { return fmaf(a, b, -c * d); }
+  __device__ static __forceinline__ float dadd(float a, float b, float c, float d) { return fmaf(a, b, c * d); }
+};
+template <> struct Ar<df> {
+  __device__ static __forceinline__ df add(df a, df b) { return a + b; }
+  __device__ static __forceinline__ df sub(df a, df b) { return a - b; }
+  __device__ static __forceinline__ df mul(df a, df b) { return a * b; }
+  __device__ static __forceinline__ df neg(df a) { return -a; }
+  __device__ static __forceinline__ df half(df a) { return df_half(a); }
+  __device__ static __forceinline__ df zero() { return df{0.0f, 0.0f}; }
+  // hi/lo splits of 1/sqrt(2), sqrt(3)/2 and sqrt(2)
+  __device__ static __forceinline__ df sqrt1_2() { return df{0x1.6a09e6p-1f, 0x1.9fcef4p-27f}; }
+  __device__ static __forceinline__ df sqrt3_2() { return df{0x1.bb67aep-1f, 0x1.0b0996p-26f}; }
+  __device__ static __forceinline__ df sqrt2() { return df{0x1.6a09e6p+0f, 0x1.9fcef4p-26f}; }
+  __device__ static __forceinline__ df dsub(df a, df b, df c, df d) { return dot2_sub(a, b, c, d); }
+  __device__ static __forceinline__ df dadd(df a, df b, df c, df d) { return dot2_add(a, b, c, d); }
+};
+
+// ------------------------------------------------------------------ complex
+template <class R> struct alignas(2 * sizeof(R)) cx {
+  R re, im;
+};
+template <class R> __device__ __forceinline__ cx<R> cadd(cx<R> a, cx<R> b) {
+  return {Ar<R>::add(a.re, b.re), Ar<R>::add(a.im, b.im)};
+}
+template <class R> __device__ __forceinline__ cx<R> csub(cx<R> a, cx<R> b) {
+  return {Ar<R>::sub(a.re, b.re), Ar<R>::sub(a.im, b.im)};
+}
+template <class R> __device__ __forceinline__ cx<R> cmul(cx<R> a, cx<R> b) {
+  return {Ar<R>::dsub(a.re, b.re, a.im, b.im), Ar<R>::dadd(a.re, b.im, a.im, b.re)};
+}
+// a * conj(b)
+template <class R> __device__ __forceinline__ cx<R> cmulc(cx<R> a, cx<R> b) {
+  return {Ar<R>::dadd(a.re, b.re, a.im, b.im), Ar<R>::dsub(a.im, b.re, a.re, b.im)};
+}
+template <class R> __device__ __forceinline__ cx<R> cconj(cx<R> a) { return {a.re, Ar<R>::neg(a.im)}; }
+// multiply by -i (forward) or +i (inverse)
+template <class R, bool INV> __device__ __forceinline__ cx<R> cmul_mi(cx<R> a) {
+  if (INV) return {Ar<R>::neg(a.im), a.re};
+  return {a.im, Ar<R>::neg(a.re)};
+}
+template <class R> __device__ __forceinline__ cx<R> chalf(cx<R> a) { return {Ar<R>::half(a.re), Ar<R>::half(a.im)}; }
+template <class R> __device__ __forceinline__ cx<R> cscale(cx<R> a, R s) { return {Ar<R>::mul(a.re, s), Ar<R>::mul(a.im, s)}; }
+
+// --------------------------------------------------------- storage <-> R
+// Storage kinds: IO_F64 (double), IO_F32 (float), SP_DF (float2 hi/lo pair), SP_F32 (float).
+template <class R, class S> struct Io;
+template <> struct Io<df, double> {
+  __device__ static __forceinline__ df ld(const double* p, long long i) { return df_from_double(__ldg(p + i)); }
+  __device__ static __forceinline__ void st(double* p, long long i, df v) { p[i] = df_to_double(v); }
+};
+template <> struct Io<df, float2> {
+  __device__ static __forceinline__ df ld(const float2* p, long long i) { float2 v = p[i]; return df{v.x, v.y}; }
+  __device__ static __forceinline__ void st(float2* p, long long i, df v) { p[i] = make_float2(v.hi, v.lo); }
+};
+template <> struct Io<df, float> {
+  __device__ static __forceinline__ df ld(const float* p, long long i) { return df{p[i], 0.0f}; }
+  __device__ static __forceinline__ void st(float* p, long long i, df v) { p[i] = df_to_f32(v); }
+};
+template <> struct Io<float, double> {
+  __device__ static __forceinline__ float ld(const double* p, long long i) { return f32_from_double(__ldg(p + i)); }
+  __device__ static __forceinline__ void st(double* p, long long i, float v) { p[i] = double_from_f32(v); }
+};
+template <> struct Io<float, float> {
+  __device__ static __forceinline__ float ld(const float* p, long long i) { return p[i]; }
+  __device__ static __forceinline__ void st(float* p, long long i, float v) { p[i] = v; }
+};
+
+}  // namespace pp

@@ -1,0 +1,148 @@
+// pp_fft.cuh -- shared-memory mixed-radix (2,3,4,8) Stockham FFT for a batch of lines.
+//
+// The complex DFT Y_k = sum_n z_n exp(-2 pi i n k / M) (Sec. "Periodic Boundary Condition")
+// of every line of a CTA is computed in place in shared memory by the Stockham
+// autosort recursion: with current length n = M/s and radix r (m = n/r), stage
+// butterfly (p, q), p < m, q < s, reads z[q + s(p + u m)], u < r, applies an r-point
+// DFT and the twiddle exp(-2 pi i p t / n) = w_M^(p t s), and writes y[q + s(r p + t)].
+// After the last stage the result is in natural order.  Each thread holds all of its
+// butterflies of a stage in registers between two barriers, so the stage can be done in
+// place; the host sizes the batch so that a stage never needs more than NB(r)
+// butterflies per thread.
+#pragma once
+#include "pp_arith.cuh"
+
+namespace pp {
+
+constexpr int kMaxStages = 16;
+
+// butterflies per thread per stage
+template <int RAD> struct NBut;
+template <> struct NBut<2> { static constexpr int v = 4; };
+template <> struct NBut<3> { static constexpr int v = 2; };
+template <> struct NBut<4> { static constexpr int v = 2; };
+template <> struct NBut<8> { static constexpr int v = 1; };
+// complex values a thread holds per stage: 8 for radix 2/4/8, 6 for radix 3
+constexpr int kCapPerThread = 8;
+constexpr int kCapPerThread3 = 6;
+
+// r-point DFTs in registers (forward kernel exp(-2 pi i/r); INV uses the conjugate).
+template <class R, bool INV> __device__ __forceinline__ void dft2(cx<R>* a) {
+  cx<R> t = a[0];
+  a[0] = cadd(t, a[1]);
+  a[1] = csub(t, a[1]);
+}
+template <class R, bool INV> __device__ __forceinline__ void dft4(cx<R>* a) {
+  cx<R> t0 = cadd(a[0], a[2]), t1 = csub(a[0], a[2]);
+  cx<R> t2 = cadd(a[1], a[3]), t3 = cmul_mi<R, INV>(csub(a[1], a[3]));
+  a[0] = cadd(t0, t2);
+  a[2] = csub(t0, t2);
+  a[1] = cadd(t1, t3);
+  a[3] = csub(t1, t3);
+}
+template <class R, bool INV> __device__ __forceinline__ void dft3(cx<R>* a) {
+  cx<R> t1 = cadd(a[1], a[2]);
+  cx<R> d = csub(a[1], a[2]);
+  // t2 = (a1 - a2) * (-+ i sqrt(3)/2)
+  cx<R> t2 = cmul_mi<R, INV>(cscale(d, Ar<R>::sqrt3_2()));
+  cx<R> m = csub(a[0], chalf(t1));
+  a[0] = cadd(a[0], t1);
+  a[1] = cadd(m, t2);
+  a[2] = csub(m, t2);
+}
+template <class R, bool INV> __device__ __forceinline__ void dft8(cx<R>* a) {
+  cx<R> e[4] = {a[0], a[2], a[4], a[6]};
+  cx<R> o[4] = {a[1], a[3], a[5], a[7]};
+  dft4<R, INV>(e);
+  dft4<R, INV>(o);
+  // o1 *= w8, o2 *= w8^2 = -+i, o3 *= w8^3 ; w8 = exp(-+ i pi/4) = (1 -+ i)/sqrt2
+  const R s = Ar<R>::sqrt1_2();
+  {
+    cx<R> v = o[1];
+    // (re + im*i)(1 - i)/sqrt2 = ((re + im) + (im - re) i)/sqrt2   [forward]
+    // (re + im*i)(1 + i)/sqrt2 = ((re - im) + (im + re) i)/sqrt2   [inverse]
+    cx<R> w = INV ? cx<R>{Ar<R>::sub(v.re, v.im), Ar<R>::add(v.im, v.re)}
+                  : cx<R>{Ar<R>::add(v.re, v.im), Ar<R>::sub(v.im, v.re)};
+    o[1] = cscale(w, s);
+  }
+  o[2] = cmul_mi<R, INV>(o[2]);
+  {
+    cx<R> v = o[3];
+    // w8^3 = (-1 - i)/sqrt2 [fwd]: (re + im i)(-1 - i) = (-re + im) + (-im - re) i
+    // conj: (-1 + i)/sqrt2 [inv]: (re + im i)(-1 + i) = (-re - im) + (re - im) i
+    cx<R> w = INV ? cx<R>{Ar<R>::neg(Ar<R>::add(v.re, v.im)), Ar<R>::sub(v.re, v.im)}
+                  : cx<R>{Ar<R>::sub(v.im, v.re), Ar<R>::neg(Ar<R>::add(v.im, v.re))};
+    o[3] = cscale(w, s);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    a[k] = cadd(e[k], o[k]);
+    a[k + 4] = csub(e[k], o[k]);
+  }
+}
+
+template <class R, int RAD, bool INV> __device__ __forceinline__ void dft_r(cx<R>* a) {
+  if (RAD == 2) dft2<R, INV>(a);
+  else if (RAD == 3) dft3<R, INV>(a);
+  else if (RAD == 4) dft4<R, INV>(a);
+  else dft8<R, INV>(a);
+}
+
+// One Stockham stage over all lines of the CTA.  buf: lines of M complex at stride ldm.
+// tw: w_M^j = exp(-2 pi i j / M), j < M (shared memory).
+template <class R, int RAD, bool INV>
+__device__ __forceinline__ void fft_stage(cx<R>* buf, int nlines, int M, int ldm, int s, const cx<R>* tw) {
+  constexpr int NB = NBut<RAD>::v;
+  const int nbl = M / RAD;
+  const int total = nlines * nbl;
+  cx<R> a[NB][RAD];
+#pragma unroll
+  for (int i = 0; i < NB; i++) {
+    int b = threadIdx.x + i * blockDim.x;
+    if (b < total) {
+      int line = b / nbl, j = b - line * nbl;
+      const cx<R>* x = buf + line * ldm + j;
+#pragma unroll
+      for (int u = 0; u < RAD; u++) a[i][u] = x[u * nbl];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NB; i++) {
+    int b = threadIdx.x + i * blockDim.x;
+    if (b < total) {
+      int line = b / nbl, j = b - line * nbl;
+      int p = j / s, q = j - p * s;
+      dft_r<R, RAD, INV>(a[i]);
+      cx<R>* y = buf + line * ldm + q + s * RAD * p;
+      y[0] = a[i][0];
+#pragma unroll
+      for (int t = 1; t < RAD; t++) {
+        cx<R> w = tw[p * t * s];
+        y[s * t] = INV ? cmulc(a[i][t], w) : cmul(a[i][t], w);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+struct FftPlan {
+  int M;              // complex length
+  int nst;            // number of stages
+  int rad[kMaxStages];
+};
+
+template <class R, bool INV>
+__device__ void fft_lines(cx<R>* buf, int nlines, int ldm, const FftPlan& fp, const cx<R>* tw) {
+  int s = 1;
+  for (int st = 0; st < fp.nst; st++) {
+    int r = fp.rad[st];
+    if (r == 8) fft_stage<R, 8, INV>(buf, nlines, fp.M, ldm, s, tw);
+    else if (r == 4) fft_stage<R, 4, INV>(buf, nlines, fp.M, ldm, s, tw);
+    else if (r == 3) fft_stage<R, 3, INV>(buf, nlines, fp.M, ldm, s, tw);
+    else fft_stage<R, 2, INV>(buf, nlines, fp.M, ldm, s, tw);
+    s *= r;
+  }
+}
+
+}  // namespace pp

@@ -1,0 +1,126 @@
+// pp_internal.h -- plan and kernel-argument structures shared by the host code and the kernels.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pp_fft.cuh"
+#include "pittpack_gb.h"
+
+namespace pp {
+
+// Per-axis transform family (Table "Summary of the appropriate Fourier transformations",
+// plus the type-IV pair for an axis with a Dirichlet face at one end and Neumann at the other).
+enum AxisKind { AX_P = 0, AX_NN = 1, AX_DD = 2, AX_DN = 3, AX_ND = 4 };
+
+// Line transform kinds.
+enum LineKind {
+  LK_R2C = 0,   // real N -> N/2+1 complex, forward DFT (periodic)
+  LK_C2R = 1,   // N/2+1 complex -> real N, unnormalised Hermitian synthesis
+  LK_C2C_F = 2, // complex N -> complex N, forward
+  LK_C2C_I = 3, // complex N -> complex N, unnormalised inverse
+  LK_DCT2 = 4,  // Neumann forward  ("DCT10")
+  LK_DCT3 = 5,  // Neumann inverse  ("DCT01"), Y0 + 2 sum_{k>0} Yk cos(...)
+  LK_DST2 = 6,  // Dirichlet forward ("DST10")
+  LK_DST3 = 7,  // Dirichlet inverse ("DST01"), (-1)^n Y_{N-1} + 2 sum_{k<N-1} Yk sin(...)
+  LK_DCT4 = 8,  // Neumann-low / Dirichlet-high, self-inverse up to 2/N
+  LK_DST4 = 9,  // Dirichlet-low / Neumann-high, self-inverse up to 2/N
+};
+
+// Arguments of one batched line-transform launch.  All offsets and strides are in
+// "real" storage units of the respective array (a complex element is 2 consecutive reals).
+struct LineArgs {
+  const void* in;
+  void* out;
+  int N;              // line length (reals for real kinds, complex count for C2C)
+  int kind;           // LineKind
+  int nlines;         // total lines of the launch
+  int lpc;            // lines per CTA
+  int ldm;            // shared-memory stride of one line (complex elements)
+  int lines_per_plane;
+  int parts;          // 2: a complex column split into re/im real lines
+  long long in_plane, out_plane;
+  long long in_line, out_line;  // stride between consecutive (column/row) lines
+  long long in_pos, out_pos;    // stride between consecutive positions along a line
+  const void* tw;     // stage twiddles w_M^j, j < M (complex, arithmetic type)
+  const void* aux;    // pre/post twiddles (complex, arithmetic type), layout per kind
+  FftPlan fp;
+};
+
+// Per-mode z-solve descriptor (tables computed on the host in FP64).
+struct ZMode {
+  int woff, wlen;     // prefix of Thomas multipliers w_k in the w table
+  int qoff, qlen;     // periodic z: prefix of q = A'^{-1} e_0
+  float winf[2];      // converged multiplier (hi, lo)
+  float wlast[2];     // multiplier of the last row
+  float gam[2];       // periodic: gamma
+  float igam[2];      // periodic: 1/gamma
+  float dsm[2];       // periodic: 1 / (1 + z_0 + z_{n-1}/gamma)
+  int flags;          // ZF_* bits
+  int pad;
+};
+enum { ZF_PERIODIC = 1, ZF_SINGULAR = 2 };
+
+struct ZArgs {
+  void* data;             // spectral array, in place
+  long long plane;        // reals per z-plane
+  int nz;
+  int cplx;               // 1: consecutive real pairs share a mode
+  long long nreal;        // reals per plane that carry modes
+  const ZMode* modes;
+  const float2* wtab;     // (hi, lo) multipliers
+  const float2* qtab;     // (hi, lo) periodic end-solution prefix
+  float scale[2];         // dz^2 * inverse-transform weights (hi, lo)
+  int transpose;          // 1: solve with the transposed factorisation (adjoint)
+};
+
+}  // namespace pp
+
+// Plan object behind the opaque C handle.
+struct pp_plan {
+  int nx, ny, nz;
+  int bc[6];
+  double dx, dy, dz;
+  int dtype;        // pp_dtype
+  int kx, ky;       // AxisKind
+  int layout;       // 0: x periodic (complex after x); 1: y periodic only; 2: both real
+  bool singular;
+  // spectral sizes, in reals
+  long long xrow;       // reals per row after the x transform
+  long long xplane;     // reals per plane after the x transform
+  long long splane;     // reals per plane of the fully transformed array
+  size_t elem;          // bytes per spill real (8: df pair, 4: float)
+  void* bufA;
+  void* bufB;
+  size_t buf_bytes;
+  // tables
+  void* d_tw_x; void* d_aux_x; void* d_tw_y; void* d_aux_y;
+  pp::FftPlan fx, fy;
+  pp::ZMode* d_modes;
+  float2* d_wtab;
+  float2* d_qtab;
+  long long nmodes;
+  double zscale;
+  // launch shapes
+  int threads_x, lpc_x, ldm_x;
+  int threads_y, lpc_y, ldm_y;
+  size_t smem_x, smem_y;
+  // mixed-precision refinement scratch
+  void* d_resid;       // residual / correction (FP64 I/O size)
+  void* d_mean;        // kMeanParts partial sums + 1 mean (float2 each), singular refinement
+  void* d_host_f;      // device staging for host-buffer solves
+  void* d_host_u;
+  int* d_status;
+};
+
+namespace pp {
+// launchers (return cudaError_t of the launch)
+cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_out, const void* in, void* out,
+                         cudaStream_t st);
+cudaError_t launch_zsolve(const pp_plan* p, void* data, int transpose, cudaStream_t st);
+cudaError_t launch_residual(const pp_plan* p, const void* f, const void* u, void* r, cudaStream_t st);
+cudaError_t launch_add(const pp_plan* p, void* u, const void* d, const void* shift, cudaStream_t st);
+// mean of an FP64 grid: nparts block sums into `partials` (nparts float2), result (hi,lo) into `mean`
+cudaError_t launch_mean(const pp_plan* p, const void* u, void* partials, int nparts, void* mean, cudaStream_t st);
+constexpr int kMeanParts = 1024;
+}  // namespace pp

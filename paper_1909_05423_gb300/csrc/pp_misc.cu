@@ -1,0 +1,131 @@
+// pp_misc.cu -- residual and update kernels of the mixed-precision refinement step.
+//
+// r = f - A_h u with the cell-centred 7-point stencil (Sec. "Mathematical Formulation") and the
+// face ghost rules (periodic wrap, Neumann u[-1] = u[0], homogeneous Dirichlet u[-1] = -u[0]),
+// evaluated in double-float arithmetic on FP64 data; then u += delta.
+#include "pp_internal.h"
+
+namespace pp {
+
+struct ResArgs {
+  const double* f;
+  const double* u;
+  double* r;
+  int nx, ny, nz;
+  int bc[6];
+  float ix2[2], iy2[2], iz2[2];  // 1/h^2 as (hi, lo)
+};
+
+__device__ __forceinline__ df ghost_or(int bc, df c) { return bc == 1 ? c : -c; }
+
+__global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long nxy = (long long)a.nx * a.ny;
+  long long n = nxy * a.nz;
+  if (p >= n) return;
+  int k = (int)(p / nxy);
+  long long rem = p - (long long)k * nxy;
+  int j = (int)(rem / a.nx);
+  int i = (int)(rem - (long long)j * a.nx);
+  const double* u = a.u;
+  df c = df_from_double(__ldg(u + p));
+  df xm, xp, ym, yp, zm, zp;
+  if (i > 0) xm = df_from_double(__ldg(u + p - 1));
+  else xm = (a.bc[0] == 0) ? df_from_double(__ldg(u + p + a.nx - 1)) : ghost_or(a.bc[0], c);
+  if (i < a.nx - 1) xp = df_from_double(__ldg(u + p + 1));
+  else xp = (a.bc[1] == 0) ? df_from_double(__ldg(u + p - (a.nx - 1))) : ghost_or(a.bc[1], c);
+  if (j > 0) ym = df_from_double(__ldg(u + p - a.nx));
+  else ym = (a.bc[2] == 0) ? df_from_double(__ldg(u + p + (long long)(a.ny - 1) * a.nx)) : ghost_or(a.bc[2], c);
+  if (j < a.ny - 1) yp = df_from_double(__ldg(u + p + a.nx));
+  else yp = (a.bc[3] == 0) ? df_from_double(__ldg(u + p - (long long)(a.ny - 1) * a.nx)) : ghost_or(a.bc[3], c);
+  if (k > 0) zm = df_from_double(__ldg(u + p - nxy));
+  else zm = (a.bc[4] == 0) ? df_from_double(__ldg(u + p + (long long)(a.nz - 1) * nxy)) : ghost_or(a.bc[4], c);
+  if (k < a.nz - 1) zp = df_from_double(__ldg(u + p + nxy));
+  else zp = (a.bc[5] == 0) ? df_from_double(__ldg(u + p - (long long)(a.nz - 1) * nxy)) : ghost_or(a.bc[5], c);
+  df c2 = c + c;
+  df lap = ((xm + xp) - c2) * df{a.ix2[0], a.ix2[1]} + ((ym + yp) - c2) * df{a.iy2[0], a.iy2[1]} +
+           ((zm + zp) - c2) * df{a.iz2[0], a.iz2[1]};
+  df r = df_from_double(__ldg(a.f + p)) - lap;
+  a.r[p] = df_to_double(r);
+}
+
+// u += d (- shift, the mean of u, when the problem is singular and the result must be mean-free)
+__global__ void __launch_bounds__(256) k_add(double* u, const double* d, long long n, const float2* shift) {
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  df v = df_from_double(u[p]) + df_from_double(__ldg(d + p));
+  if (shift) v = v - df{shift->x, shift->y};
+  u[p] = df_to_double(v);
+}
+
+// Block partial sums of an FP64 grid in double-float arithmetic (first pass of the mean).
+constexpr int kSumThreads = 256;
+__global__ void __launch_bounds__(kSumThreads) k_partial_sum(const double* u, long long n, float2* part) {
+  __shared__ df sh[kSumThreads];
+  df acc = df{0.f, 0.f};
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x)
+    acc = acc + df_from_double(__ldg(u + p));
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sh[threadIdx.x] = sh[threadIdx.x] + sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = make_float2(sh[0].hi, sh[0].lo);
+}
+
+// Second pass: mean = (sum of partials) / n, one block.
+__global__ void __launch_bounds__(kSumThreads) k_finish_mean(const float2* part, int nparts, float inv_n_hi,
+                                                              float inv_n_lo, float2* mean) {
+  __shared__ df sh[kSumThreads];
+  df acc = df{0.f, 0.f};
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc = acc + df{part[i].x, part[i].y};
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sh[threadIdx.x] = sh[threadIdx.x] + sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    df m = sh[0] * df{inv_n_hi, inv_n_lo};
+    *mean = make_float2(m.hi, m.lo);
+  }
+}
+
+static void split_h(double v, float* o) {
+  float h = (float)v;
+  o[0] = h;
+  o[1] = (float)(v - (double)h);
+}
+
+cudaError_t launch_residual(const pp_plan* p, const void* f, const void* u, void* r, cudaStream_t st) {
+  ResArgs a;
+  a.f = (const double*)f; a.u = (const double*)u; a.r = (double*)r;
+  a.nx = p->nx; a.ny = p->ny; a.nz = p->nz;
+  for (int i = 0; i < 6; i++) a.bc[i] = p->bc[i];
+  split_h(1.0 / (p->dx * p->dx), a.ix2);
+  split_h(1.0 / (p->dy * p->dy), a.iy2);
+  split_h(1.0 / (p->dz * p->dz), a.iz2);
+  long long n = (long long)p->nx * p->ny * p->nz;
+  k_residual<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mean(const pp_plan* p, const void* u, void* partials, int nparts, void* mean, cudaStream_t st) {
+  long long n = (long long)p->nx * p->ny * p->nz;
+  k_partial_sum<<<nparts, kSumThreads, 0, st>>>((const double*)u, n, (float2*)partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  float inv[2];
+  split_h(1.0 / (double)n, inv);
+  k_finish_mean<<<1, kSumThreads, 0, st>>>((const float2*)partials, nparts, inv[0], inv[1], (float2*)mean);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add(const pp_plan* p, void* u, const void* d, const void* shift, cudaStream_t st) {
+  long long n = (long long)p->nx * p->ny * p->nz;
+  k_add<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((double*)u, (const double*)d, n, (const float2*)shift);
+  return cudaGetLastError();
+}
+
+}  // namespace pp

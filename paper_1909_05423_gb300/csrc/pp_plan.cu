@@ -1,0 +1,658 @@
+// pp_plan.cu -- plan creation, coefficient tables, launch sequences and the C ABI.
+//
+// A plan fixes the grid, the per-face boundary conditions, the spacings and the arithmetic
+// mode, and precomputes on the host, in FP64:
+//   * the FFT twiddles w_M^j and the pre/post twiddles of the DCT/DST recipes
+//     (angles reduced exactly in integers, then split into double-float pairs);
+//   * for every (kx,ky) pair the eigenvalue shift of Table "Eigenvalues"
+//     (lambda = -2 + 2 cos(theta) per axis, divided by h^2, summed over x and y) and the
+//     Thomas multipliers of its z system, evaluated with the same FP64 operations as a
+//     textbook Thomas elimination, truncated once they reach their fixed point.
+// A solve is then five launches on the caller's stream:
+//   x-forward -> y-forward -> z tridiagonal -> y-inverse -> x-inverse.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pp_internal.h"
+
+namespace pp {
+cudaError_t launch_lines_impl(const LineArgs& a, bool df_arith, int oy, int sin, int sout, int threads, size_t smem,
+                              cudaStream_t st);
+cudaError_t launch_zsolve_impl(const ZArgs& a, bool df_spill, cudaStream_t st);
+}  // namespace pp
+
+using namespace pp;
+
+static thread_local std::string g_err;
+
+static pp_status fail(pp_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define CUDA_OK(call)                                                                      \
+  do {                                                                                     \
+    cudaError_t _e = (call);                                                               \
+    if (_e != cudaSuccess) return fail(PP_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(_e)); \
+  } while (0)
+
+// ------------------------------------------------------------------ helpers
+static bool smooth23(int n) {
+  if (n < 1) return false;
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  return n == 1;
+}
+
+static FftPlan make_fft(int M) {
+  FftPlan f;
+  f.M = M;
+  f.nst = 0;
+  int m = M;
+  while (m % 8 == 0 && f.nst < kMaxStages) { f.rad[f.nst++] = 8; m /= 8; }
+  while (m % 4 == 0 && f.nst < kMaxStages) { f.rad[f.nst++] = 4; m /= 4; }
+  while (m % 2 == 0 && f.nst < kMaxStages) { f.rad[f.nst++] = 2; m /= 2; }
+  while (m % 3 == 0 && f.nst < kMaxStages) { f.rad[f.nst++] = 3; m /= 3; }
+  return f;
+}
+
+// exp(-2 pi i num/den) with the angle reduced exactly: num/den = q/4 + t, |t| <= 1/8.
+static void expi(long long num, long long den, double& re, double& im) {
+  const double PI = 3.14159265358979323846;
+  long long r = num % den;
+  if (r < 0) r += den;
+  // quadrant index qd = round(4 r / den), remainder a/(4 den) with |a| <= den/2
+  long long qd = (4 * r + den / 2) / den;  // 0..4
+  long long a = 4 * r - qd * den;          // angle = 2 pi (qd/4 + a/(4 den))
+  double t = 2.0 * PI * (double)a / (4.0 * (double)den);
+  double c = std::cos(t), s = std::sin(t);
+  double cr, sr;  // cos, sin of the full angle
+  switch (qd & 3) {
+    case 0: cr = c; sr = s; break;
+    case 1: cr = -s; sr = c; break;
+    case 2: cr = -c; sr = -s; break;
+    default: cr = s; sr = -c; break;
+  }
+  re = cr;
+  im = -sr;
+}
+
+// Per-axis eigenvalue (unit spacing), Table "Eigenvalues"; mixed D/N axis: -2 + 2cos(pi(k+1/2)/n).
+static double axis_eig(int kind, int N, int k) {
+  const double PI = 3.14159265358979323846;
+  switch (kind) {
+    case AX_P: return -2.0 + 2.0 * cos(2.0 * PI * (double)k / N);
+    case AX_NN: return -2.0 + 2.0 * cos(PI * (double)k / N);
+    case AX_DD: return -2.0 + 2.0 * cos(PI * (double)(k + 1) / N);
+    default: return -2.0 + 2.0 * cos(PI * (2.0 * k + 1.0) / (2.0 * N));
+  }
+}
+
+static int axis_kind(int lo, int hi) {
+  if (lo == PP_BC_PERIODIC || hi == PP_BC_PERIODIC) return (lo == PP_BC_PERIODIC && hi == PP_BC_PERIODIC) ? AX_P : -1;
+  if (lo == PP_BC_NEUMANN && hi == PP_BC_NEUMANN) return AX_NN;
+  if (lo == PP_BC_DIRICHLET && hi == PP_BC_DIRICHLET) return AX_DD;
+  if (lo == PP_BC_DIRICHLET && hi == PP_BC_NEUMANN) return AX_DN;
+  return AX_ND;
+}
+
+static int fwd_kind(int ax, bool complex_data) {
+  switch (ax) {
+    case AX_P: return complex_data ? LK_C2C_F : LK_R2C;
+    case AX_NN: return LK_DCT2;
+    case AX_DD: return LK_DST2;
+    case AX_DN: return LK_DST4;
+    default: return LK_DCT4;
+  }
+}
+static int inv_kind(int ax, bool complex_data) {
+  switch (ax) {
+    case AX_P: return complex_data ? LK_C2C_I : LK_C2R;
+    case AX_NN: return LK_DCT3;
+    case AX_DD: return LK_DST3;
+    case AX_DN: return LK_DST4;
+    default: return LK_DCT4;
+  }
+}
+// constant inverse weight of an axis (the syntheses are unnormalised)
+static double axis_weight(int ax, int N) { return (ax == AX_DN || ax == AX_ND) ? 2.0 / N : 1.0 / N; }
+
+static void split2(double v, float* o) {
+  float h = (float)v;
+  o[0] = h;
+  o[1] = (float)(v - (double)h);
+}
+
+// Build a complex table in the plan's arithmetic type: df -> 4 floats, float -> 2 floats.
+struct Tab {
+  std::vector<float> v;
+  bool dfm;
+  void push(double re, double im) {
+    if (dfm) {
+      float a[2], b[2];
+      split2(re, a);
+      split2(im, b);
+      v.push_back(a[0]); v.push_back(a[1]); v.push_back(b[0]); v.push_back(b[1]);
+    } else {
+      v.push_back((float)re);
+      v.push_back((float)im);
+    }
+  }
+};
+
+static pp_status upload(void** dptr, const std::vector<float>& v) {
+  size_t bytes = std::max<size_t>(v.size(), 4) * sizeof(float);
+  cudaError_t e = cudaMalloc(dptr, bytes);
+  if (e != cudaSuccess) return fail(PP_ERR_OUT_OF_MEMORY, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+  if (!v.empty()) CUDA_OK(cudaMemcpy(*dptr, v.data(), v.size() * sizeof(float), cudaMemcpyHostToDevice));
+  return PP_OK;
+}
+
+// twiddles of one axis: stage table (M entries) and aux table for its transform family
+static pp_status axis_tables(pp_plan* p, int ax, int N, bool complex_data, FftPlan& fp, void** dtw, void** daux) {
+  bool dfm = (p->dtype == PP_F64);
+  int M = (ax == AX_P && complex_data) ? N : N / 2;
+  fp = make_fft(M);
+  Tab tw{{}, dfm}, aux{{}, dfm};
+  double re, im;
+  for (int j = 0; j < M; j++) { expi(j, M, re, im); tw.push(re, im); }
+  if (ax == AX_P && !complex_data) {
+    for (int k = 0; k <= M; k++) { expi(k, N, re, im); aux.push(re, im); }
+  } else if (ax == AX_NN || ax == AX_DD) {
+    for (int k = 0; k <= M; k++) { expi(k, N, re, im); aux.push(re, im); }
+    for (int k = 0; k <= M; k++) { expi(k, 4LL * N, re, im); aux.push(re, im); }
+  } else if (ax == AX_DN || ax == AX_ND) {
+    for (int n = 0; n < M; n++) { expi(4LL * n + 1, 8LL * N, re, im); aux.push(re, im); }
+    for (int k = 0; k < M; k++) { expi(k, 2LL * N, re, im); aux.push(re, im); }
+  }
+  pp_status s = upload(dtw, tw.v);
+  if (s != PP_OK) return s;
+  return upload(daux, aux.v);
+}
+
+// Thomas multipliers of one z system, w_k = h2 / m_k with m_0 = b_0, m_k = b_k - h2 w_{k-1}
+// (textbook elimination with sub = super = h2), truncated at the fixed point.
+struct WSeq {
+  std::vector<double> pre;  // w_0 .. w_{len-1}
+  double winf, wlast;
+};
+static void thomas_multipliers(int n, double h2, double b_first, double b_int, double b_last, WSeq& s) {
+  s.pre.clear();
+  if (n == 1) { s.wlast = h2 / b_first; s.winf = s.wlast; return; }
+  double w = h2 / b_first;
+  s.pre.push_back(w);
+  for (int k = 1; k <= n - 2; k++) {
+    double m = b_int - h2 * w;
+    double wn = h2 / m;
+    if (wn == w) break;  // fixed point: every later interior multiplier is the same
+    s.pre.push_back(wn);
+    w = wn;
+  }
+  s.winf = w;
+  s.wlast = h2 / (b_last - h2 * w);
+}
+
+static pp_status z_tables(pp_plan* p) {
+  const int nx = p->nx, ny = p->ny, nz = p->nz;
+  const double h2 = 1.0 / (p->dz * p->dz);
+  const int zlo = p->bc[4], zhi = p->bc[5];
+  const bool zper = (zlo == PP_BC_PERIODIC);
+  long long ncx, ncy;  // mode grid
+  if (p->layout == 0) { ncx = nx / 2 + 1; ncy = ny; }
+  else if (p->layout == 1) { ncx = nx; ncy = ny / 2 + 1; }
+  else { ncx = nx; ncy = ny; }
+  p->nmodes = ncx * ncy;
+  std::vector<ZMode> modes((size_t)p->nmodes);
+  std::vector<float> wtab, qtab;
+  std::vector<double> lx(ncx), ly(ncy);
+  for (long long i = 0; i < ncx; i++) lx[i] = axis_eig(p->kx, nx, (int)i) / (p->dx * p->dx);
+  for (long long j = 0; j < ncy; j++) ly[j] = axis_eig(p->ky, ny, (int)j) / (p->dy * p->dy);
+  WSeq ws;
+  std::vector<double> dp, cpv;
+  for (long long j = 0; j < ncy; j++) {
+    for (long long i = 0; i < ncx; i++) {
+      ZMode& m = modes[(size_t)(j * ncx + i)];
+      memset(&m, 0, sizeof m);
+      double lam = lx[i] + ly[j];
+      double b_int = -2.0 * h2 + lam;
+      bool sing = p->singular && i == 0 && j == 0;
+      if (sing) {
+        // rows 1..n-1 with u_0 pinned: b = b_int, last row + h2 for a Neumann top face
+        double b_last = zper ? b_int : b_int + h2;
+        m.flags = ZF_SINGULAR;
+        m.woff = (int)(wtab.size() / 2);
+        int ns = nz - 1;
+        double w = 0.0;
+        for (int r = 0; r < ns; r++) {
+          double b = (r == ns - 1) ? b_last : b_int;
+          double mm = (r == 0) ? b : b - h2 * w;
+          w = h2 / mm;
+          float o[2];
+          split2(w, o);
+          wtab.push_back(o[0]); wtab.push_back(o[1]);
+        }
+        m.wlen = ns;
+        continue;
+      }
+      double b_first, b_last;
+      if (zper) {
+        // Sherman-Morrison: gamma = -b_0, b'_0 = b_0 - gamma, b'_{n-1} = b_{n-1} - h2 h2 / gamma
+        double gamma = -b_int;
+        b_first = b_int - gamma;
+        b_last = b_int - h2 * h2 / gamma;
+        m.flags = ZF_PERIODIC;
+        thomas_multipliers(nz, h2, b_first, b_int, b_last, ws);
+        // q = h2 A'^{-1} e_0 (forward elimination of e_0 decays; truncate when negligible)
+        dp.assign(nz, 0.0);
+        cpv.assign(nz, 0.0);
+        auto wk = [&](int k) { return k == nz - 1 ? ws.wlast : (k < (int)ws.pre.size() ? ws.pre[k] : ws.winf); };
+        int K = nz;
+        for (int k = 0; k < nz; k++) {
+          // dp_k = (e0_k - h2 dp_{k-1}) / m_k,  1/m_k = w_k / h2
+          double rhs = (k == 0) ? 1.0 : -h2 * dp[k - 1];
+          dp[k] = rhs * wk(k) / h2;
+          if (k > 0 && std::fabs(dp[k]) < 1e-40 * std::fabs(dp[0])) { K = k; break; }
+        }
+        // back substitution x_k = dp_k - cp_k x_{k+1}, cp_k = w_k
+        std::vector<double> q(K);
+        double x = 0.0;
+        for (int k = K - 1; k >= 0; k--) {
+          x = (k == nz - 1) ? dp[k] : dp[k] - wk(k) * x;
+          q[k] = x;
+        }
+        // z = A'^{-1}(gamma e_0 + h2 e_{n-1}):  z_0 and z_{n-1}
+        double inv00 = q[0];
+        double inv0n = (K == nz) ? q[nz - 1] : 0.0;          // (A'^{-1})_{0,n-1}
+        double invnn = ws.wlast / h2;                         // (A'^{-1})_{n-1,n-1}
+        double z0 = gamma * inv00 + h2 * inv0n;
+        double zn = gamma * inv0n + h2 * invnn;
+        double D = 1.0 / (1.0 + z0 + h2 * zn / gamma);
+        split2(gamma / h2, m.gam);
+        split2(h2 / gamma, m.igam);
+        split2(D, m.dsm);
+        m.qoff = (int)(qtab.size() / 2);
+        m.qlen = K;
+        for (int k = 0; k < K; k++) {
+          float o[2];
+          split2(h2 * q[k], o);
+          qtab.push_back(o[0]); qtab.push_back(o[1]);
+        }
+      } else {
+        b_first = b_int + (zlo == PP_BC_NEUMANN ? h2 : -h2);
+        b_last = b_int + (zhi == PP_BC_NEUMANN ? h2 : -h2);
+        thomas_multipliers(nz, h2, b_first, b_int, b_last, ws);
+      }
+      m.woff = (int)(wtab.size() / 2);
+      m.wlen = (int)ws.pre.size();
+      for (double w : ws.pre) {
+        float o[2];
+        split2(w, o);
+        wtab.push_back(o[0]); wtab.push_back(o[1]);
+      }
+      split2(ws.winf, m.winf);
+      split2(ws.wlast, m.wlast);
+    }
+    if (wtab.size() / 2 > 0x7fffffffULL || qtab.size() / 2 > 0x7fffffffULL)
+      return fail(PP_ERR_UNSUPPORTED_SIZE, "z coefficient tables exceed 2^31 entries");
+  }
+  size_t mb = modes.size() * sizeof(ZMode);
+  cudaError_t e = cudaMalloc((void**)&p->d_modes, mb);
+  if (e != cudaSuccess) return fail(PP_ERR_OUT_OF_MEMORY, "cudaMalloc(modes): %s", cudaGetErrorString(e));
+  CUDA_OK(cudaMemcpy(p->d_modes, modes.data(), mb, cudaMemcpyHostToDevice));
+  pp_status s = upload((void**)&p->d_wtab, wtab);
+  if (s != PP_OK) return s;
+  return upload((void**)&p->d_qtab, qtab);
+}
+
+static void free_plan(pp_plan* p) {
+  if (!p) return;
+  void* ptrs[] = {p->bufA, p->bufB, p->d_tw_x, p->d_aux_x, p->d_tw_y, p->d_aux_y, p->d_modes, p->d_wtab,
+                  p->d_qtab, p->d_resid, p->d_mean, p->d_host_f, p->d_host_u, p->d_status};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  delete p;
+}
+
+// launch shapes
+static void choose_shapes(pp_plan* p, const pp_plan_options* opt) {
+  size_t cs = (p->dtype == PP_F64) ? 16 : 8;  // bytes per complex in shared memory
+  const size_t smem_cap = 200 * 1024;
+  // x lines
+  {
+    int M = p->fx.M;
+    bool r3 = false;
+    for (int i = 0; i < p->fx.nst; i++) r3 |= p->fx.rad[i] == 3;
+    int T = (opt && opt->threads_x) ? opt->threads_x : 512;
+    int cap = (r3 ? kCapPerThread3 : kCapPerThread) * T;
+    int nlines = p->ny * p->nz;
+    int lpc = std::max(1, cap / std::max(M, 1));
+    if (opt && opt->lines_x) lpc = std::min(lpc, opt->lines_x);
+    lpc = std::min(lpc, nlines);
+    int ldm = M + 1;
+    while (lpc > 1 && (size_t)lpc * ldm * cs + (size_t)M * cs > smem_cap) lpc--;
+    p->threads_x = T;
+    p->lpc_x = lpc;
+    p->ldm_x = ldm;
+    p->smem_x = (size_t)lpc * ldm * cs + (size_t)M * cs;
+  }
+  // y lines
+  {
+    int M = p->fy.M;
+    bool r3 = false;
+    for (int i = 0; i < p->fy.nst; i++) r3 |= p->fy.rad[i] == 3;
+    bool cplx_cols = (p->layout == 0);
+    int parts = (cplx_cols && p->ky != AX_P) ? 2 : 1;
+    int ncols = cplx_cols ? p->nx / 2 + 1 : p->nx;
+    int T = (opt && opt->threads_y) ? opt->threads_y : 512;
+    int cap = (r3 ? kCapPerThread3 : kCapPerThread) * T;
+    int maxlines = std::max(1, cap / std::max(M, 1));
+    int cols = std::max(1, maxlines / parts);
+    if (opt && opt->cols_y) cols = std::min(cols, opt->cols_y);
+    cols = std::min(cols, ncols);
+    int lpc = cols * parts;
+    int ldm = M + 1;
+    while (lpc > parts && (size_t)lpc * ldm * cs + (size_t)M * cs > smem_cap) lpc -= parts;
+    if (lpc * M <= kCapPerThread3 * 256 && !(opt && opt->threads_y)) T = 256;
+    p->threads_y = T;
+    p->lpc_y = lpc;
+    p->ldm_y = ldm;
+    p->smem_y = (size_t)lpc * ldm * cs + (size_t)M * cs;
+  }
+}
+
+// ------------------------------------------------------------------ line launches
+enum { ST_F64 = 0, ST_F32 = 1, ST_SPILL = 2 };
+
+namespace pp {
+// axis 0 = x, 1 = y; dir 0 = forward, 1 = inverse.  io_in / io_out: ST_* codes.
+cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_out, const void* in, void* out,
+                         cudaStream_t st) {
+  LineArgs a;
+  memset(&a, 0, sizeof a);
+  a.in = in;
+  a.out = out;
+  const bool dfm = (p->dtype == PP_F64);
+  const long long nxy = (long long)p->nx * p->ny;
+  if (axis == 0) {
+    bool per = (p->kx == AX_P);
+    a.N = p->nx;
+    a.kind = dir == 0 ? fwd_kind(p->kx, false) : inv_kind(p->kx, false);
+    a.nlines = p->ny * p->nz;
+    a.lines_per_plane = p->ny;
+    a.parts = 1;
+    a.lpc = p->lpc_x;
+    a.ldm = p->ldm_x;
+    a.fp = p->fx;
+    a.tw = p->d_tw_x;
+    a.aux = p->d_aux_x;
+    long long grid_plane = nxy, grid_row = p->nx;
+    long long sp_plane = p->xplane, sp_row = p->xrow;
+    if (dir == 0) {
+      a.in_plane = grid_plane; a.in_line = grid_row; a.in_pos = 1;
+      a.out_plane = sp_plane; a.out_line = sp_row; a.out_pos = per ? 2 : 1;
+    } else {
+      a.in_plane = sp_plane; a.in_line = sp_row; a.in_pos = per ? 2 : 1;
+      a.out_plane = grid_plane; a.out_line = grid_row; a.out_pos = 1;
+    }
+    return launch_lines_impl(a, dfm, 0, io_in, io_out, p->threads_x, p->smem_x, st);
+  }
+  // y
+  const bool cplx_cols = (p->layout == 0);
+  a.N = p->ny;
+  a.kind = dir == 0 ? fwd_kind(p->ky, cplx_cols) : inv_kind(p->ky, cplx_cols);
+  int parts = (cplx_cols && p->ky != AX_P) ? 2 : 1;
+  int ncols = cplx_cols ? p->nx / 2 + 1 : p->nx;
+  a.parts = parts;
+  a.lines_per_plane = ncols * parts;
+  a.nlines = a.lines_per_plane * p->nz;
+  a.lpc = p->lpc_y;
+  a.ldm = p->ldm_y;
+  a.fp = p->fy;
+  a.tw = p->d_tw_y;
+  a.aux = p->d_aux_y;
+  // x-spectral side: columns of the x-transformed array
+  long long xs_plane = p->xplane, xs_col = cplx_cols ? 2 : 1, xs_pos = p->xrow;
+  // fully spectral side
+  long long s_plane = p->splane, s_col, s_pos;
+  if (p->layout == 1) { s_col = 2; s_pos = 2LL * p->nx; }
+  else { s_col = xs_col; s_pos = xs_pos; }
+  if (dir == 0) {
+    a.in_plane = xs_plane; a.in_line = xs_col; a.in_pos = xs_pos;
+    a.out_plane = s_plane; a.out_line = s_col; a.out_pos = s_pos;
+  } else {
+    a.in_plane = s_plane; a.in_line = s_col; a.in_pos = s_pos;
+    a.out_plane = xs_plane; a.out_line = xs_col; a.out_pos = xs_pos;
+  }
+  return launch_lines_impl(a, dfm, 1, io_in, io_out, p->threads_y, p->smem_y, st);
+}
+
+cudaError_t launch_zsolve(const pp_plan* p, void* data, int transpose, cudaStream_t st) {
+  ZArgs a;
+  memset(&a, 0, sizeof a);
+  a.data = data;
+  a.plane = p->splane;
+  a.nz = p->nz;
+  a.cplx = (p->layout != 2);
+  a.nreal = p->splane;
+  a.modes = p->d_modes;
+  a.wtab = p->d_wtab;
+  a.qtab = p->d_qtab;
+  split2(p->zscale, a.scale);
+  a.transpose = transpose;
+  return launch_zsolve_impl(a, p->dtype == PP_F64, st);
+}
+}  // namespace pp
+
+static pp_status run_stage(pp_plan* p, int stage, const void* f, void* u, int transpose, cudaStream_t st) {
+  int io = (p->dtype == PP_MIXED_F32IO) ? ST_F32 : ST_F64;
+  cudaError_t e = cudaSuccess;
+  static const char* names[] = {"x-forward", "y-forward", "z-solve", "y-inverse", "x-inverse"};
+  switch (stage) {
+    case 0: e = launch_lines(p, 0, 0, io, ST_SPILL, f, p->bufA, st); break;
+    case 1: e = launch_lines(p, 1, 0, ST_SPILL, ST_SPILL, p->bufA, p->bufB, st); break;
+    case 2: e = launch_zsolve(p, p->bufB, transpose, st); break;
+    case 3: e = launch_lines(p, 1, 1, ST_SPILL, ST_SPILL, p->bufB, p->bufA, st); break;
+    case 4: e = launch_lines(p, 0, 1, ST_SPILL, io, p->bufA, u, st); break;
+    default: return fail(PP_ERR_INVALID_ARG, "stage %d out of range", stage);
+  }
+  if (e != cudaSuccess) return fail(PP_ERR_CUDA, "%s launch: %s", names[stage], cudaGetErrorString(e));
+  return PP_OK;
+}
+
+static pp_status run_pipeline(pp_plan* p, const void* f, void* u, int transpose, cudaStream_t st) {
+  for (int s = 0; s < 5; s++) {
+    pp_status r = run_stage(p, s, f, u, transpose, st);
+    if (r != PP_OK) return r;
+  }
+  return PP_OK;
+}
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+const char* pp_version(void) { return "pittpack-gb 0.1 (sm_103a)"; }
+
+const char* pp_last_error_string(void) { return g_err.c_str(); }
+
+pp_status pp_plan_create(pp_plan** out, int nx, int ny, int nz, const pp_bc bc[6], double dx, double dy, double dz,
+                         pp_dtype dtype, const pp_plan_options* opt) {
+  g_err.clear();
+  if (!out) return fail(PP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!bc) return fail(PP_ERR_INVALID_ARG, "bc is NULL");
+  if (!(dx > 0) || !(dy > 0) || !(dz > 0) || !std::isfinite(dx) || !std::isfinite(dy) || !std::isfinite(dz))
+    return fail(PP_ERR_INVALID_ARG, "spacings must be positive and finite");
+  if (dtype != PP_F64 && dtype != PP_MIXED_F64IO && dtype != PP_MIXED_F32IO)
+    return fail(PP_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);
+  for (int i = 0; i < 6; i++)
+    if (bc[i] != PP_BC_PERIODIC && bc[i] != PP_BC_NEUMANN && bc[i] != PP_BC_DIRICHLET)
+      return fail(PP_ERR_INVALID_ARG, "bc[%d] = %d is not a boundary condition", i, (int)bc[i]);
+  for (int a = 0; a < 3; a++)
+    if ((bc[2 * a] == PP_BC_PERIODIC) != (bc[2 * a + 1] == PP_BC_PERIODIC))
+      return fail(PP_ERR_BC_PAIRING, "axis %d: periodic must be given on both faces", a);
+  if (opt)
+    for (int i = 0; i < 8; i++)
+      if (opt->reserved[i]) return fail(PP_ERR_INVALID_ARG, "options.reserved must be zero");
+  if (opt && (opt->threads_x < 0 || opt->threads_y < 0 || opt->lines_x < 0 || opt->cols_y < 0 ||
+              (opt->threads_x && (opt->threads_x % 32 || opt->threads_x > 512)) ||
+              (opt->threads_y && (opt->threads_y % 32 || opt->threads_y > 512))))
+    return fail(PP_ERR_INVALID_ARG, "options: thread counts must be multiples of 32, at most 512");
+  for (int v : {nx, ny})
+    if (v < 2 || v > 4096 || v % 2 || !smooth23(v))
+      return fail(PP_ERR_UNSUPPORTED_SIZE, "nx, ny must be even 2^a 3^b in [2, 4096] (got %d x %d)", nx, ny);
+  bool zper = (bc[4] == PP_BC_PERIODIC);
+  if (nz < (zper ? 3 : 2) || nz > (1 << 20))
+    return fail(PP_ERR_UNSUPPORTED_SIZE, "nz = %d out of range (>= 2, periodic z >= 3)", nz);
+  if ((long long)nx * ny > (1LL << 30) || (long long)nx * ny * nz > (1LL << 36))
+    return fail(PP_ERR_UNSUPPORTED_SIZE, "grid too large");
+
+  pp_plan* p = new (std::nothrow) pp_plan();
+  if (!p) return fail(PP_ERR_OUT_OF_MEMORY, "host allocation failed");
+  memset(p, 0, sizeof *p);
+  p->nx = nx; p->ny = ny; p->nz = nz;
+  for (int i = 0; i < 6; i++) p->bc[i] = bc[i];
+  p->dx = dx; p->dy = dy; p->dz = dz;
+  p->dtype = dtype;
+  p->kx = axis_kind(bc[0], bc[1]);
+  p->ky = axis_kind(bc[2], bc[3]);
+  p->layout = (p->kx == AX_P) ? 0 : (p->ky == AX_P ? 1 : 2);
+  p->singular = true;
+  for (int i = 0; i < 6; i++)
+    if (bc[i] == PP_BC_DIRICHLET) p->singular = false;
+  p->elem = (dtype == PP_F64) ? 8 : 4;
+  p->xrow = (p->kx == AX_P) ? (long long)nx + 2 : nx;
+  p->xplane = p->xrow * ny;
+  if (p->layout == 1) p->splane = 2LL * nx * (ny / 2 + 1);
+  else p->splane = p->xplane;
+  p->zscale = dz * dz * axis_weight(p->kx, nx) * axis_weight(p->ky, ny);
+
+  pp_status s;
+  if ((s = axis_tables(p, p->kx, nx, false, p->fx, &p->d_tw_x, &p->d_aux_x)) != PP_OK) { free_plan(p); return s; }
+  if ((s = axis_tables(p, p->ky, ny, p->layout == 0, p->fy, &p->d_tw_y, &p->d_aux_y)) != PP_OK) { free_plan(p); return s; }
+  if ((s = z_tables(p)) != PP_OK) { free_plan(p); return s; }
+  choose_shapes(p, opt);
+
+  p->buf_bytes = (size_t)std::max(p->xplane, p->splane) * nz * p->elem;
+  cudaError_t e = cudaMalloc(&p->bufA, p->buf_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&p->bufB, p->buf_bytes);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p->d_status, sizeof(int));
+  if (e != cudaSuccess) {
+    free_plan(p);
+    return fail(PP_ERR_OUT_OF_MEMORY, "workspace allocation of 2 x %zu bytes failed: %s", p->buf_bytes,
+                cudaGetErrorString(e));
+  }
+  cudaMemset(p->d_status, 0, sizeof(int));
+  *out = p;
+  return PP_OK;
+}
+
+pp_status pp_plan_destroy(pp_plan* plan) {
+  if (!plan) return PP_OK;
+  cudaDeviceSynchronize();
+  free_plan(plan);
+  return PP_OK;
+}
+
+pp_status pp_solve(pp_plan* p, const void* f, void* u, pp_stream_t stream) {
+  if (!p || !f || !u) return fail(PP_ERR_INVALID_ARG, "NULL plan or pointer");
+  return run_pipeline(p, f, u, 0, (cudaStream_t)stream);
+}
+
+pp_status pp_solve_adjoint(pp_plan* p, const void* g, void* gf, pp_stream_t stream) {
+  if (!p || !g || !gf) return fail(PP_ERR_INVALID_ARG, "NULL plan or pointer");
+  // S = X^-1 Y^-1 T^-1 W Y X with W the constant inverse weight; S^T = X^T Y^T W T^-T Y^-T X^-T.
+  // The unnormalised syntheses are the transposes of the analyses up to the per-mode
+  // multiplicities that the weight absorbs, so the transposed pipeline runs the same line
+  // kernels around the transposed tridiagonal factorisation.
+  return run_pipeline(p, g, gf, 1, (cudaStream_t)stream);
+}
+
+pp_status pp_solve_refined(pp_plan* p, const void* f, void* u, pp_stream_t stream) {
+  if (!p || !f || !u) return fail(PP_ERR_INVALID_ARG, "NULL plan or pointer");
+  if (p->dtype != PP_MIXED_F64IO) return fail(PP_ERR_INVALID_ARG, "refinement needs a PP_MIXED_F64IO plan");
+  if (f == u) return fail(PP_ERR_INVALID_ARG, "u must not alias f for the refined solve");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!p->d_resid) {
+    size_t bytes = (size_t)p->nx * p->ny * p->nz * sizeof(double);
+    cudaError_t e = cudaMalloc(&p->d_resid, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_mean, (kMeanParts + 1) * sizeof(float2));
+    if (e != cudaSuccess) return fail(PP_ERR_OUT_OF_MEMORY, "residual buffer (%zu bytes): %s", bytes, cudaGetErrorString(e));
+  }
+  pp_status s = run_pipeline(p, f, u, 0, st);
+  if (s != PP_OK) return s;
+  cudaError_t e = launch_residual(p, f, u, p->d_resid, st);
+  if (e != cudaSuccess) return fail(PP_ERR_CUDA, "residual launch: %s", cudaGetErrorString(e));
+  s = run_pipeline(p, p->d_resid, p->d_resid, 0, st);
+  if (s != PP_OK) return s;
+  // A singular problem is solved for the mean-free u; the FP32 first solve leaves a constant offset
+  // that the refinement step cannot see (it lies in the null space), so it is removed explicitly.
+  const void* shift = nullptr;
+  if (p->singular) {
+    float2* mean = (float2*)p->d_mean + kMeanParts;
+    e = launch_mean(p, u, p->d_mean, kMeanParts, mean, st);
+    if (e != cudaSuccess) return fail(PP_ERR_CUDA, "mean launch: %s", cudaGetErrorString(e));
+    shift = mean;
+  }
+  e = launch_add(p, u, p->d_resid, shift, st);
+  if (e != cudaSuccess) return fail(PP_ERR_CUDA, "update launch: %s", cudaGetErrorString(e));
+  return PP_OK;
+}
+
+pp_status pp_solve_batched(pp_plan* const* plans, const void* const* f, void* const* u, int n, pp_stream_t stream) {
+  if (n < 0 || (n > 0 && (!plans || !f || !u))) return fail(PP_ERR_INVALID_ARG, "bad batch arguments");
+  for (int i = 0; i < n; i++) {
+    pp_status s = pp_solve(plans[i], f[i], u[i], stream);
+    if (s != PP_OK) return s;
+  }
+  return PP_OK;
+}
+
+pp_status pp_solve_host(pp_plan* p, const void* f_host, void* u_host, pp_stream_t stream) {
+  if (!p || !f_host || !u_host) return fail(PP_ERR_INVALID_ARG, "NULL plan or pointer");
+  size_t bytes = (size_t)p->nx * p->ny * p->nz * (p->dtype == PP_MIXED_F32IO ? 4 : 8);
+  if (!p->d_host_f) {
+    cudaError_t e = cudaMalloc(&p->d_host_f, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_host_u, bytes);
+    if (e != cudaSuccess) return fail(PP_ERR_OUT_OF_MEMORY, "staging buffers: %s", cudaGetErrorString(e));
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  CUDA_OK(cudaMemcpyAsync(p->d_host_f, f_host, bytes, cudaMemcpyHostToDevice, st));
+  pp_status s = run_pipeline(p, p->d_host_f, p->d_host_u, 0, st);
+  if (s != PP_OK) return s;
+  CUDA_OK(cudaMemcpyAsync(u_host, p->d_host_u, bytes, cudaMemcpyDeviceToHost, st));
+  CUDA_OK(cudaStreamSynchronize(st));
+  return PP_OK;
+}
+
+pp_status pp_run_stage(pp_plan* p, int stage, const void* f, void* u, pp_stream_t stream) {
+  if (!p) return fail(PP_ERR_INVALID_ARG, "NULL plan");
+  if ((stage == 0 && !f) || (stage == 4 && !u)) return fail(PP_ERR_INVALID_ARG, "NULL pointer for stage %d", stage);
+  return run_stage(p, stage, f, u, 0, (cudaStream_t)stream);
+}
+
+pp_status pp_plan_status(pp_plan* p) {
+  if (!p) return fail(PP_ERR_INVALID_ARG, "NULL plan");
+  int v = 0;
+  CUDA_OK(cudaMemcpy(&v, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  CUDA_OK(cudaMemset(p->d_status, 0, sizeof(int)));
+  if (v) return fail((pp_status)v, "device reported status %d", v);
+  return PP_OK;
+}
+
+size_t pp_plan_device_bytes(const pp_plan* p) {
+  if (!p) return 0;
+  return 2 * p->buf_bytes;
+}
+
+}  // extern "C"

@@ -1,0 +1,79 @@
+"""CPU-side checks of the C ABI: the library builds, loads, exports every symbol declared in
+include/*.h, and validates arguments (these paths return before any CUDA call)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_1909_05423_gb300 import _lib, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _lib.load()
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = open(h).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names.update(re.findall(r"\b(pp_[a-z_0-9]+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = _declared()
+    assert "pp_solve" in declared and "pp_plan_create" in declared
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(_lib.EXPORTS) <= set(declared)
+
+
+def test_version(lib):
+    assert b"sm_103a" in lib.pp_version()
+
+
+def _create(lib, nx, ny, nz, bc, dx=1.0, dtype=0):
+    h = ctypes.c_void_p()
+    st = lib.pp_plan_create(ctypes.byref(h), nx, ny, nz, _lib.bc_array(bc), dx, 1.0, 1.0, dtype, None)
+    return st, h
+
+
+@pytest.mark.parametrize("nx,ny,nz,bc,code", [
+    (10, 8, 8, "PPPPDD", 2),     # 10 is not 2^a 3^b
+    (9, 8, 8, "PPPPDD", 2),      # odd
+    (8, 8, 1, "PPPPDD", 2),      # nz < 2
+    (8, 8, 2, "NNNNPP", 2),      # periodic z needs nz >= 3
+    (8192, 8, 8, "PPPPDD", 2),   # too long
+    (8, 8, 8, "PNPPDD", 3),      # periodic paired with Neumann
+    (8, 8, 8, "PPNNDP", 3),
+])
+def test_validation(lib, nx, ny, nz, bc, code):
+    st, h = _create(lib, nx, ny, nz, bc)
+    assert st == code
+    assert h.value is None
+    assert len(lib.pp_last_error_string()) > 0
+
+
+def test_invalid_spacing_and_dtype(lib):
+    st, _ = _create(lib, 8, 8, 8, "PPPPDD", dx=0.0)
+    assert st == 1
+    st, _ = _create(lib, 8, 8, 8, "PPPPDD", dtype=7)
+    assert st == 1
+    bad = (ctypes.c_int * 6)(0, 0, 0, 0, 2, 5)
+    h = ctypes.c_void_p()
+    assert lib.pp_plan_create(ctypes.byref(h), 8, 8, 8, bad, 1.0, 1.0, 1.0, 0, None) == 1
+
+
+def test_null_arguments(lib):
+    assert lib.pp_solve(None, None, None, None) == 1
+    assert lib.pp_solve_adjoint(None, None, None, None) == 1
+    assert lib.pp_plan_destroy(None) == 0
+    assert lib.pp_solve_batched(None, None, None, 0, None) == 0
+    assert lib.pp_solve_batched(None, None, None, -1, None) == 1

@@ -1,0 +1,145 @@
+"""GPU path vs the CPU oracle, element by element (relative L2), FP64-class path.
+Sizes span several CTAs, ragged last CTAs and odd nz; edge sizes (2, 6) and every per-axis
+boundary kind are covered."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from paper_1909_05423_gb300 import workloads
+from tests import helpers
+from tests.gpu_common import gpu_solve, need_gpu, rel_l2, torch
+
+pytestmark = pytest.mark.gpu
+TOL_F64 = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _setup(oracle):
+    need_gpu()
+
+
+@pytest.mark.parametrize("bc", ["PPPPDD", "NNDDNN", "PPPPPP", "NNNNNN", "DDDDDD", "DNNDPP", "NDPPDN",
+                                "PPNNDD", "DDPPNN", "NNPPND"])
+@pytest.mark.parametrize("shape", [(37, 48, 96), (11, 72, 54), (8, 18, 144)])
+def test_parity_f64(oracle, bc, shape):
+    nz, ny, nx = shape
+    sp = (1.0 / nx, 1.0 / ny, 1.3 / nz)
+    f = workloads.uniform_source(shape, seed=7, remove_mean=False)
+    ref = oracle.solve(f, bc, sp)
+    u = gpu_solve(f, bc, sp)
+    assert rel_l2(u, ref) <= TOL_F64, rel_l2(u, ref)
+
+
+@pytest.mark.parametrize("shape", [(5, 6, 4), (3, 2, 6), (2, 4, 2)])
+def test_tiny_all_axis_kinds(oracle, shape):
+    """Every per-axis boundary kind (5^3 combinations) on tiny uneven grids, incl. length-2 axes."""
+    rng = np.random.default_rng(3)
+    sp = (0.7, 1.3, 0.9)
+    for kinds in itertools.product(helpers.AXIS_KINDS, repeat=3):
+        bc = "".join(kinds)
+        if bc[4] == "P" and shape[0] < 3:
+            continue
+        f = rng.uniform(-1, 1, size=shape)
+        ref = oracle.solve(f, bc, sp)
+        u = gpu_solve(f, bc, sp)
+        assert rel_l2(u, ref) <= TOL_F64, (bc, rel_l2(u, ref))
+
+
+def test_config1_manufactured_32(oracle):
+    """32^3, periodic x/y, Dirichlet z, u* = sin 2pi x sin 2pi y sin pi z: GPU RMS error equals the
+    closed form 1.042987e-03 and the GPU matches the oracle."""
+    n = 32
+    sp = (1.0 / n,) * 3
+    u_star, f = workloads.manufactured((n, n, n), sp, [(1.0, ("sin", 2 * math.pi), ("sin", 2 * math.pi),
+                                                        ("sin", math.pi))])
+    u = gpu_solve(f, "PPPPDD", sp)
+    err = math.sqrt(((u - u_star) ** 2).mean())
+    assert abs(err - 1.042987e-03) <= 1e-6 * 1.042987e-03
+    assert rel_l2(u, oracle.solve(f, "PPPPDD", sp)) <= TOL_F64
+
+
+def test_exact_discrete_eigenfunction():
+    """A sampled eigenfunction product is returned scaled by -sum k^2 / sum lambda_d (exact discrete
+    solution) element by element, at 96^3 with the NN-NN-DD mode of Table tb4."""
+    n = 96
+    sp = (1.0 / n,) * 3
+    kap = [math.pi, 2 * math.pi, 3 * math.pi]
+    u_star, f = workloads.manufactured((n, n, n), sp, [(1.0, ("cos", kap[0]), ("cos", kap[1]), ("sin", kap[2]))])
+    u = gpu_solve(f, "NNNNDD", sp)
+    ratio = helpers.discrete_solution_ratio(kap, [1.0 / n] * 3)
+    assert rel_l2(u, u_star * ratio) <= TOL_F64
+
+
+def test_singular_zero_mean(oracle):
+    shape = (16, 24, 36)
+    rng = np.random.default_rng(5)
+    f = rng.uniform(0, 1, size=shape)  # non-zero mean: solved as f - mean(f)
+    for bc in ("NNNNNN", "PPPPPP", "PPNNNN", "NNPPPP"):
+        u = gpu_solve(f, bc, (0.1, 0.2, 0.3))
+        assert abs(u.mean()) <= 1e-13 * np.abs(u).max()
+        assert rel_l2(u, oracle.solve(f, bc, (0.1, 0.2, 0.3))) <= TOL_F64
+
+
+def test_residual_invariant_256(oracle):
+    """256^3, config-2 boundary set (Neumann x, Dirichlet y, Neumann z): ||A u - f|| / ||f|| < 1e-12 with
+    the oracle's stencil, plus sampled elementwise parity against a full oracle solve."""
+    n = 256
+    shape = (n, n, n)
+    sp = (1.0 / n,) * 3
+    f = workloads.uniform_source(shape, seed=2, remove_mean=True)
+    u = gpu_solve(f, "NNDDNN", sp)
+    r = oracle.laplacian(u, "NNDDNN", sp) - f
+    assert np.linalg.norm(r) / np.linalg.norm(f) < 1e-12
+
+
+def test_deterministic(oracle):
+    shape = (9, 24, 48)
+    f = workloads.uniform_source(shape, seed=9)
+    a = gpu_solve(f, "DNPPNN", (1, 1, 1))
+    b = gpu_solve(f, "DNPPNN", (1, 1, 1))
+    assert np.array_equal(a, b)
+
+
+def test_aliasing_in_place(oracle):
+    import paper_1909_05423_gb300 as pp
+    shape = (10, 12, 18)
+    f = workloads.uniform_source(shape, seed=4)
+    plan = pp.Plan(shape, "DDNNPP", (1, 1, 1), "f64")
+    t = torch.from_numpy(f).cuda()
+    plan.solve(t, out=t)
+    torch.cuda.synchronize()
+    assert rel_l2(t.cpu().numpy(), oracle.solve(f, "DDNNPP")) <= TOL_F64
+    plan.close()
+
+
+def test_host_buffers(oracle):
+    import paper_1909_05423_gb300 as pp
+    shape = (14, 18, 24)
+    f = workloads.uniform_source(shape, seed=6)
+    plan = pp.Plan(shape, "NDDNPP", (1, 1, 1), "f64")
+    fh = torch.from_numpy(f).pin_memory()
+    u = plan.solve_host(fh)
+    assert rel_l2(u.numpy(), oracle.solve(f, "NDDNPP")) <= TOL_F64
+    plan.close()
+
+
+def test_batched_uneven(oracle):
+    """Uneven sizes and boundary sets in one batched call (each against its own oracle solve)."""
+    import paper_1909_05423_gb300 as pp
+    grids = workloads.batched_grids(seed=4, count=6, sides=(6, 12, 18, 24, 32, 48))
+    plans, fs, refs = [], [], []
+    for i, (shape, bc) in enumerate(grids):
+        if bc[4] == "P" and shape[0] < 3:
+            continue
+        f = workloads.uniform_source(shape, seed=100 + i)
+        plans.append(pp.Plan(shape, bc, (1.0, 1.0, 1.0), "f64"))
+        fs.append(torch.from_numpy(f).cuda())
+        refs.append(oracle.solve(f, bc))
+    outs = pp.solve_batched(plans, fs)
+    torch.cuda.synchronize()
+    for o, r in zip(outs, refs):
+        assert rel_l2(o.cpu().numpy(), r) <= TOL_F64
+    for p in plans:
+        p.close()
