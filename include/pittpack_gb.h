@@ -103,6 +103,23 @@ pp_status pp_solve(pp_plan* plan, const void* f_dev, void* u_dev, pp_stream_t st
  * (PP_ERR_INVALID_ARG otherwise).  u must not alias f. */
 pp_status pp_solve_refined(pp_plan* plan, const void* f_dev, void* u_dev, pp_stream_t stream);
 
+/* pp_solve_refined without any device allocation.  (The paper has no counterpart: it is an
+ * addition for callers that cannot allocate device memory when they solve -- code running
+ * while a stream is captured into a CUDA graph, where cudaMalloc is refused; time-stepping
+ * loops that must not allocate mid-run; applications whose own allocator owns the GPU.)
+ * pp_solve_refined allocates a grid-sized residual buffer on its first call; this entry point
+ * instead uses a fixed 16 MiB device array inside the library (held by every GPU that loads the
+ * library until the process exits) plus the plan's own workspace.
+ *   plan   : a PP_MIXED_F64IO plan (created beforehand; creating a plan does allocate)
+ *   f_dev  : input, nx*ny*nz doubles on the device; u_dev: output, same size, must not alias f
+ * Limit: nx*ny*nz <= 2,097,152 cells (16 MiB of FP64), else PP_ERR_UNSUPPORTED_SIZE with a
+ * message; other errors as pp_solve_refined.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress), so make that first call before any stream
+ * capture.  All calls share the one array and each call overwrites what it reads, so calls
+ * that may overlap on the GPU (different streams, or different host threads) race: serialise
+ * them.  Asynchronous on stream like pp_solve. */
+pp_status pp_solve_refined_noalloc(pp_plan* plan, const void* f_dev, void* u_dev, pp_stream_t stream);
+
 /* Solve n independent problems, plans[i] applied to (f[i] -> u[i]), enqueued back to
  * back on one stream (each plan owns its workspace, so the solves do not interfere).
  * Errors as pp_solve; the first failing index stops the enqueueing. */

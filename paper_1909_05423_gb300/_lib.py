@@ -19,7 +19,7 @@ BC_CODE = {"P": 0, "N": 1, "D": 2}
 DTYPES = {"f64": 0, "mixed_f64io": 1, "mixed_f32io": 2}
 
 # every entry point declared in include/pittpack_gb.h
-EXPORTS = ["pp_plan_create", "pp_solve", "pp_solve_refined", "pp_solve_batched", "pp_solve_adjoint",
+EXPORTS = ["pp_plan_create", "pp_solve", "pp_solve_refined", "pp_solve_refined_noalloc", "pp_solve_batched", "pp_solve_adjoint",
            "pp_solve_host", "pp_run_stage", "pp_plan_destroy", "pp_plan_status", "pp_plan_device_bytes", "pp_last_error_string",
            "pp_version"]
 
@@ -54,7 +54,8 @@ def load():
                                        ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_int, ctypes.POINTER(PlanOptions)]
         lib.pp_plan_create.restype = ctypes.c_int
-        for name in ("pp_solve", "pp_solve_refined", "pp_solve_adjoint", "pp_solve_host"):
+        for name in ("pp_solve", "pp_solve_refined", "pp_solve_refined_noalloc", "pp_solve_adjoint",
+                     "pp_solve_host"):
             fn = getattr(lib, name)
             fn.argtypes = [vp, vp, vp, vp]
             fn.restype = ctypes.c_int

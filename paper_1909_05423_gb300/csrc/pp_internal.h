@@ -123,4 +123,6 @@ cudaError_t launch_add(const pp_plan* p, void* u, const void* d, const void* shi
 // mean of an FP64 grid: nparts block sums into `partials` (nparts float2), result (hi,lo) into `mean`
 cudaError_t launch_mean(const pp_plan* p, const void* u, void* partials, int nparts, void* mean, cudaStream_t st);
 constexpr int kMeanParts = 1024;
+// record the calling thread's error detail (returned by pp_last_error_string) and return s
+__attribute__((visibility("hidden"))) pp_status set_last_error(pp_status s, const char* msg);
 }  // namespace pp

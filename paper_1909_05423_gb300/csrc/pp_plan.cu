@@ -41,6 +41,10 @@ static pp_status fail(pp_status s, const char* fmt, ...) {
   return s;
 }
 
+namespace pp {
+pp_status set_last_error(pp_status s, const char* msg) { return fail(s, "%s", msg); }
+}  // namespace pp
+
 #define CUDA_OK(call)                                                                      \
   do {                                                                                     \
     cudaError_t _e = (call);                                                               \
