@@ -72,7 +72,9 @@ typedef struct pp_plan_options {
   int threads_y;   /* CTA size of the y-line kernels (0 = automatic) */
   int lines_x;     /* lines per CTA, x kernels (0 = automatic) */
   int cols_y;      /* columns per CTA, y kernels (0 = automatic) */
-  int reserved[8]; /* must be zero */
+  int staged;      /* line kernels: 0 = automatic, 1 = one tile per CTA with direct loads,
+                      2 = persistent CTAs with cp.async-staged tiles */
+  int reserved[7]; /* must be zero */
 } pp_plan_options;
 
 typedef struct pp_plan pp_plan;
@@ -120,9 +122,14 @@ pp_status pp_solve_refined(pp_plan* plan, const void* f_dev, void* u_dev, pp_str
  * them.  Asynchronous on stream like pp_solve. */
 pp_status pp_solve_refined_noalloc(pp_plan* plan, const void* f_dev, void* u_dev, pp_stream_t stream);
 
-/* Solve n independent problems, plans[i] applied to (f[i] -> u[i]), enqueued back to
- * back on one stream (each plan owns its workspace, so the solves do not interfere).
- * Errors as pp_solve; the first failing index stops the enqueueing. */
+/* Solve n independent problems, plans[i] applied to (f[i] -> u[i]) -- grids of any sizes,
+ * boundary sets and dtypes -- as ONE CUDA-graph launch on `stream`.  The first call with a
+ * given (plans, f, u) list captures the n five-kernel pipelines into a graph and instantiates
+ * it (host work, a few ms); later calls with the same lists replay the cached graph (up to 8
+ * batches are cached; pp_plan_destroy evicts the graphs that use that plan).  Members run on
+ * up to 8 concurrent graph branches; members that share a plan share its workspace and run
+ * one after another on one branch.  Errors: PP_ERR_INVALID_ARG (n < 0, NULL arrays or
+ * members), PP_ERR_CUDA (capture/instantiate/launch). */
 pp_status pp_solve_batched(pp_plan* const* plans, const void* const* f, void* const* u, int n,
                            pp_stream_t stream);
 

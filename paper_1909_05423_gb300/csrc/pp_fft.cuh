@@ -16,6 +16,28 @@ namespace pp {
 
 constexpr int kMaxStages = 16;
 
+// Unsigned division by a run-time invariant divisor with one multiply-high and two shifts
+// (Granlund & Montgomery, "Division by invariant integers using multiplication", 1994):
+// l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1, q = (t + ((n - t) >> min(l,1))) >> max(l-1,0)
+// with t = mulhi(m, n); exact for all 32-bit n.
+struct FastDiv {
+  unsigned d, m, s1, s2;
+  static FastDiv make(unsigned dv) {
+    FastDiv f;
+    unsigned l = 0;
+    while ((1ull << l) < dv) l++;
+    f.d = dv;
+    f.m = (unsigned)((((1ull << 32) * ((1ull << l) - dv)) / dv) + 1);
+    f.s1 = l < 1 ? l : 1;
+    f.s2 = l > 1 ? l - 1 : 0;
+    return f;
+  }
+  __device__ __forceinline__ unsigned div(unsigned n) const {
+    unsigned t = __umulhi(m, n);
+    return (t + ((n - t) >> s1)) >> s2;
+  }
+};
+
 // butterflies per thread per stage
 template <int RAD> struct NBut;
 template <> struct NBut<2> { static constexpr int v = 4; };
@@ -91,16 +113,20 @@ template <class R, int RAD, bool INV> __device__ __forceinline__ void dft_r(cx<R
 // One Stockham stage over all lines of the CTA.  buf: lines of M complex at stride ldm.
 // tw: w_M^j = exp(-2 pi i j / M), j < M (shared memory).
 template <class R, int RAD, bool INV>
-__device__ __forceinline__ void fft_stage(cx<R>* buf, int nlines, int M, int ldm, int s, const cx<R>* tw) {
+__device__ __forceinline__ void fft_stage(cx<R>* buf, int nlines, int ldm, int s, const FastDiv& fd_nbl,
+                                          const FastDiv& fd_s, const cx<R>* tw) {
   constexpr int NB = NBut<RAD>::v;
-  const int nbl = M / RAD;
+  const int nbl = (int)fd_nbl.d;
   const int total = nlines * nbl;
   cx<R> a[NB][RAD];
+  int lj[NB];  // butterfly -> (line, j), computed once
 #pragma unroll
   for (int i = 0; i < NB; i++) {
     int b = threadIdx.x + i * blockDim.x;
+    lj[i] = -1;
     if (b < total) {
-      int line = b / nbl, j = b - line * nbl;
+      int line = (int)fd_nbl.div((unsigned)b), j = b - line * nbl;
+      lj[i] = line * ldm + j;
       const cx<R>* x = buf + line * ldm + j;
 #pragma unroll
       for (int u = 0; u < RAD; u++) a[i][u] = x[u * nbl];
@@ -109,16 +135,17 @@ __device__ __forceinline__ void fft_stage(cx<R>* buf, int nlines, int M, int ldm
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < NB; i++) {
-    int b = threadIdx.x + i * blockDim.x;
-    if (b < total) {
-      int line = b / nbl, j = b - line * nbl;
-      int p = j / s, q = j - p * s;
+    if (lj[i] >= 0) {
+      int b = threadIdx.x + i * blockDim.x;
+      int line = (int)fd_nbl.div((unsigned)b), j = b - line * nbl;
+      int p = (int)fd_s.div((unsigned)j), q = j - p * s;
       dft_r<R, RAD, INV>(a[i]);
       cx<R>* y = buf + line * ldm + q + s * RAD * p;
       y[0] = a[i][0];
+      const int ps = p * s;
 #pragma unroll
       for (int t = 1; t < RAD; t++) {
-        cx<R> w = tw[p * t * s];
+        cx<R> w = tw[ps * t];
         y[s * t] = INV ? cmulc(a[i][t], w) : cmul(a[i][t], w);
       }
     }
@@ -130,17 +157,19 @@ struct FftPlan {
   int M;              // complex length
   int nst;            // number of stages
   int rad[kMaxStages];
+  FastDiv nbl[kMaxStages];  // M / rad per stage
+  FastDiv s[kMaxStages];    // product of the earlier radices
 };
 
 template <class R, bool INV>
-__device__ void fft_lines(cx<R>* buf, int nlines, int ldm, const FftPlan& fp, const cx<R>* tw) {
+__device__ __forceinline__ void fft_lines(cx<R>* buf, int nlines, int ldm, const FftPlan& fp, const cx<R>* tw) {
   int s = 1;
   for (int st = 0; st < fp.nst; st++) {
     int r = fp.rad[st];
-    if (r == 8) fft_stage<R, 8, INV>(buf, nlines, fp.M, ldm, s, tw);
-    else if (r == 4) fft_stage<R, 4, INV>(buf, nlines, fp.M, ldm, s, tw);
-    else if (r == 3) fft_stage<R, 3, INV>(buf, nlines, fp.M, ldm, s, tw);
-    else fft_stage<R, 2, INV>(buf, nlines, fp.M, ldm, s, tw);
+    if (r == 8) fft_stage<R, 8, INV>(buf, nlines, ldm, s, fp.nbl[st], fp.s[st], tw);
+    else if (r == 4) fft_stage<R, 4, INV>(buf, nlines, ldm, s, fp.nbl[st], fp.s[st], tw);
+    else if (r == 3) fft_stage<R, 3, INV>(buf, nlines, ldm, s, fp.nbl[st], fp.s[st], tw);
+    else fft_stage<R, 2, INV>(buf, nlines, ldm, s, fp.nbl[st], fp.s[st], tw);
     s *= r;
   }
 }

@@ -40,12 +40,27 @@ struct LineArgs {
   int lines_per_plane;
   int parts;          // 2: a complex column split into re/im real lines
   long long in_plane, out_plane;
-  long long in_line, out_line;  // stride between consecutive (column/row) lines
-  long long in_pos, out_pos;    // stride between consecutive positions along a line
+  int in_line, in_pos;          // input: stride between consecutive lines / positions (reals)
+  long long out_line, out_pos;  // output: stride between consecutive lines / positions (reals)
+  int ntiles;         // tiles of the launch (x: lpc rows; y: one plane x tx columns)
+  int raw_bytes;      // bytes of one staging buffer (a raw input tile)
+  int chunk;          // 16: 16-byte asynchronous copies; 0: element-sized copies
+  int staged;         // 1: persistent CTAs with cp.async-staged tiles; 0: one tile per CTA, direct loads
+  int tx, ncols, nblk;  // y: columns per tile, columns per plane, column blocks per plane
+  int in_rows;        // y: positions staged per column
+  int raw_row;        // y: staged row length (reals)
   const void* tw;     // stage twiddles w_M^j, j < M (complex, arithmetic type)
   const void* aux;    // pre/post twiddles (complex, arithmetic type), layout per kind
   FftPlan fp;
+  FastDiv fd_kpre;    // number of pre-processing items per line (M)
+  FastDiv fd_kpost;   // number of post-processing items per line
+  FastDiv fd_lpc;     // lines per CTA
+  FastDiv fd_lpp;     // lines per plane
+  FastDiv fd_parts;   // 1 or 2
+  FastDiv fd_nblk;    // column blocks per plane
+  FastDiv fd_cpr;     // 16-byte chunks per staged row
 };
+constexpr int kMaxLpc = 512;  // lines per CTA (bounded so the per-line bases fit in shared memory)
 
 // Per-mode z-solve descriptor (tables computed on the host in FP64).
 struct ZMode {
@@ -66,7 +81,11 @@ struct ZArgs {
   long long plane;        // reals per z-plane
   int nz;
   int cplx;               // 1: consecutive real pairs share a mode
-  long long nreal;        // reals per plane that carry modes
+  long long nreal;        // reals per plane (including row padding)
+  int row_reals;          // reals per spectral row (padded)
+  int row_valid;          // reals of a row that carry modes
+  int row_modes;          // modes per row
+  FastDiv fd_row;
   const ZMode* modes;
   const float2* wtab;     // (hi, lo) multipliers
   const float2* qtab;     // (hi, lo) periodic end-solution prefix
@@ -104,7 +123,7 @@ struct pp_plan {
   // launch shapes
   int threads_x, lpc_x, ldm_x;
   int threads_y, lpc_y, ldm_y;
-  size_t smem_x, smem_y;
+  int staged;           // line-kernel variant (see LineArgs::staged)
   // mixed-precision refinement scratch
   void* d_resid;       // residual / correction (FP64 I/O size)
   void* d_mean;        // kMeanParts partial sums + 1 mean (float2 each), singular refinement

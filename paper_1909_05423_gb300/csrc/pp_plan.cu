@@ -15,6 +15,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -23,7 +24,7 @@
 
 namespace pp {
 cudaError_t launch_lines_impl(const LineArgs& a, bool df_arith, int oy, int sin, int sout, int threads, size_t smem,
-                              cudaStream_t st);
+                              int grid, cudaStream_t st);
 cudaError_t launch_zsolve_impl(const ZArgs& a, bool df_spill, cudaStream_t st);
 }  // namespace pp
 
@@ -68,6 +69,12 @@ static FftPlan make_fft(int M) {
   while (m % 4 == 0 && f.nst < kMaxStages) { f.rad[f.nst++] = 4; m /= 4; }
   while (m % 2 == 0 && f.nst < kMaxStages) { f.rad[f.nst++] = 2; m /= 2; }
   while (m % 3 == 0 && f.nst < kMaxStages) { f.rad[f.nst++] = 3; m /= 3; }
+  int s = 1;
+  for (int i = 0; i < f.nst; i++) {
+    f.nbl[i] = FastDiv::make((unsigned)(M / f.rad[i]));
+    f.s[i] = FastDiv::make((unsigned)s);
+    s *= f.rad[i];
+  }
   return f;
 }
 
@@ -328,29 +335,37 @@ static void free_plan(pp_plan* p) {
   delete p;
 }
 
-// launch shapes
+// launch shapes: threads per CTA and lines per CTA of the x and y line kernels.  Shared memory
+// per CTA = 2 staging buffers (raw tiles) + the complex work buffer + the stage twiddles.
+static size_t round16(size_t b) { return (b + 15) & ~(size_t)15; }
+
 static void choose_shapes(pp_plan* p, const pp_plan_options* opt) {
-  size_t cs = (p->dtype == PP_F64) ? 16 : 8;  // bytes per complex in shared memory
+  p->staged = (opt && opt->staged == 2) ? 1 : 0;
+  size_t cs = (p->dtype == PP_F64) ? 16 : 8;          // bytes per complex in shared memory
+  size_t se = p->elem;                                  // bytes per spill real
+  size_t ioe = (p->dtype == PP_MIXED_F32IO) ? 4 : 8;    // bytes per I/O real
   const size_t smem_cap = 200 * 1024;
-  // x lines
+  // x lines: a staged tile holds lpc rows of the wider of (grid row, spectral row)
   {
     int M = p->fx.M;
     bool r3 = false;
     for (int i = 0; i < p->fx.nst; i++) r3 |= p->fx.rad[i] == 3;
-    int T = (opt && opt->threads_x) ? opt->threads_x : 512;
+    int T = (opt && opt->threads_x) ? opt->threads_x : 128;
     int cap = (r3 ? kCapPerThread3 : kCapPerThread) * T;
     int nlines = p->ny * p->nz;
     int lpc = std::max(1, cap / std::max(M, 1));
     if (opt && opt->lines_x) lpc = std::min(lpc, opt->lines_x);
+    lpc = std::min(lpc, kMaxLpc);
     lpc = std::min(lpc, nlines);
     int ldm = M + 1;
-    while (lpc > 1 && (size_t)lpc * ldm * cs + (size_t)M * cs > smem_cap) lpc--;
+    size_t rowb = std::max((size_t)p->nx * ioe, (size_t)p->xrow * se);
+    auto need = [&](int l) { return 2 * round16((size_t)l * rowb) + (size_t)l * ldm * cs + (size_t)M * cs; };
+    while (lpc > 1 && need(lpc) > smem_cap) lpc--;
     p->threads_x = T;
     p->lpc_x = lpc;
     p->ldm_x = ldm;
-    p->smem_x = (size_t)lpc * ldm * cs + (size_t)M * cs;
   }
-  // y lines
+  // y lines: a staged tile holds up to ny rows of tx columns
   {
     int M = p->fy.M;
     bool r3 = false;
@@ -358,25 +373,50 @@ static void choose_shapes(pp_plan* p, const pp_plan_options* opt) {
     bool cplx_cols = (p->layout == 0);
     int parts = (cplx_cols && p->ky != AX_P) ? 2 : 1;
     int ncols = cplx_cols ? p->nx / 2 + 1 : p->nx;
-    int T = (opt && opt->threads_y) ? opt->threads_y : 512;
+    size_t col_bytes = (cplx_cols ? 2 : 1) * se;
+    // CTA size: 128 threads unless that leaves column segments below one 32-byte sector
+    int T = 128;
+    const int tmax = (p->dtype == PP_F64) ? 256 : 512;
+    if (opt && opt->threads_y) T = opt->threads_y;
+    else
+      while (T < tmax && (size_t)std::max(1, (kCapPerThread3 * T / std::max(M, 1)) / parts) * col_bytes < 32) T *= 2;
     int cap = (r3 ? kCapPerThread3 : kCapPerThread) * T;
     int maxlines = std::max(1, cap / std::max(M, 1));
     int cols = std::max(1, maxlines / parts);
     if (opt && opt->cols_y) cols = std::min(cols, opt->cols_y);
+    cols = std::min(cols, kMaxLpc / parts);
     cols = std::min(cols, ncols);
-    int lpc = cols * parts;
     int ldm = M + 1;
-    while (lpc > parts && (size_t)lpc * ldm * cs + (size_t)M * cs > smem_cap) lpc -= parts;
-    if (lpc * M <= kCapPerThread3 * 256 && !(opt && opt->threads_y)) T = 256;
+    // staged rows: the spectral columns of layout 1 are complex (2 reals) on the inverse side
+    size_t colr = (cplx_cols || p->layout == 1) ? 2 : 1;
+    auto need = [&](int c) {
+      return 2 * round16((size_t)p->ny * round16((size_t)c * colr * se)) + (size_t)c * parts * ldm * cs +
+             (size_t)M * cs;
+    };
+    while (cols > 1 && need(cols) > smem_cap) cols--;
     p->threads_y = T;
-    p->lpc_y = lpc;
+    p->lpc_y = cols * parts;
     p->ldm_y = ldm;
-    p->smem_y = (size_t)lpc * ldm * cs + (size_t)M * cs;
   }
 }
 
 // ------------------------------------------------------------------ line launches
 enum { ST_F64 = 0, ST_F32 = 1, ST_SPILL = 2 };
+
+// division helpers of one launch
+static void finish_args(LineArgs& a) {
+  int M = a.fp.M, N = a.N, K;
+  switch (a.kind) {
+    case LK_R2C: case LK_DCT2: case LK_DST2: K = M + 1; break;
+    case LK_C2C_F: case LK_C2C_I: K = N; break;
+    default: K = M;
+  }
+  a.fd_kpre = FastDiv::make((unsigned)M);
+  a.fd_kpost = FastDiv::make((unsigned)K);
+  a.fd_lpc = FastDiv::make((unsigned)a.lpc);
+  a.fd_lpp = FastDiv::make((unsigned)a.lines_per_plane);
+  a.fd_parts = FastDiv::make((unsigned)a.parts);
+}
 
 namespace pp {
 // axis 0 = x, 1 = y; dir 0 = forward, 1 = inverse.  io_in / io_out: ST_* codes.
@@ -387,7 +427,11 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
   a.in = in;
   a.out = out;
   const bool dfm = (p->dtype == PP_F64);
+  const size_t cs = dfm ? 16 : 8;
+  const int se = (int)p->elem;
+  const int ioe = (p->dtype == PP_MIXED_F32IO) ? 4 : 8;
   const long long nxy = (long long)p->nx * p->ny;
+  const bool in_aligned = ((uintptr_t)in % 16) == 0;
   if (axis == 0) {
     bool per = (p->kx == AX_P);
     a.N = p->nx;
@@ -402,14 +446,24 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
     a.aux = p->d_aux_x;
     long long grid_plane = nxy, grid_row = p->nx;
     long long sp_plane = p->xplane, sp_row = p->xrow;
+    int ies;  // bytes per input real
     if (dir == 0) {
-      a.in_plane = grid_plane; a.in_line = grid_row; a.in_pos = 1;
+      a.in_plane = grid_plane; a.in_line = (int)grid_row; a.in_pos = 1;
       a.out_plane = sp_plane; a.out_line = sp_row; a.out_pos = per ? 2 : 1;
+      ies = (io_in == ST_SPILL) ? se : ioe;
     } else {
-      a.in_plane = sp_plane; a.in_line = sp_row; a.in_pos = per ? 2 : 1;
+      a.in_plane = sp_plane; a.in_line = (int)sp_row; a.in_pos = per ? 2 : 1;
       a.out_plane = grid_plane; a.out_line = grid_row; a.out_pos = 1;
+      ies = se;
     }
-    return launch_lines_impl(a, dfm, 0, io_in, io_out, p->threads_x, p->smem_x, st);
+    a.ntiles = (a.nlines + a.lpc - 1) / a.lpc;
+    a.raw_bytes = (int)round16((size_t)a.lpc * a.in_line * ies);
+    a.chunk = (in_aligned && ((size_t)a.in_line * ies) % 16 == 0) ? 16 : 0;
+    a.in_rows = 0;
+    a.staged = p->staged;
+    finish_args(a);
+    size_t smem = 2 * (size_t)a.raw_bytes + (size_t)a.lpc * a.ldm * cs + (size_t)a.fp.M * cs;
+    return launch_lines_impl(a, dfm, 0, io_in, io_out, p->threads_x, smem, 0, st);
   }
   // y
   const bool cplx_cols = (p->layout == 0);
@@ -432,13 +486,30 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
   if (p->layout == 1) { s_col = 2; s_pos = 2LL * p->nx; }
   else { s_col = xs_col; s_pos = xs_pos; }
   if (dir == 0) {
-    a.in_plane = xs_plane; a.in_line = xs_col; a.in_pos = xs_pos;
+    a.in_plane = xs_plane; a.in_line = (int)xs_col; a.in_pos = (int)xs_pos;
     a.out_plane = s_plane; a.out_line = s_col; a.out_pos = s_pos;
   } else {
-    a.in_plane = s_plane; a.in_line = s_col; a.in_pos = s_pos;
+    a.in_plane = s_plane; a.in_line = (int)s_col; a.in_pos = (int)s_pos;
     a.out_plane = xs_plane; a.out_line = xs_col; a.out_pos = xs_pos;
   }
-  return launch_lines_impl(a, dfm, 1, io_in, io_out, p->threads_y, p->smem_y, st);
+  a.tx = a.lpc / parts;
+  a.ncols = ncols;
+  a.nblk = (ncols + a.tx - 1) / a.tx;
+  a.ntiles = a.nblk * p->nz;
+  a.in_rows = (a.kind == LK_C2R) ? a.fp.M + 1 : p->ny;
+  int segb = a.tx * a.in_line * se;
+  a.raw_row = (int)(round16((size_t)segb) / se);
+  a.raw_bytes = (int)round16((size_t)a.in_rows * a.raw_row * se);
+  a.chunk = (in_aligned && segb % 16 == 0 && ((size_t)a.in_pos * se) % 16 == 0 && ((size_t)a.in_plane * se) % 16 == 0)
+                ? 16 : 0;
+  a.staged = p->staged;
+  finish_args(a);
+  a.fd_nblk = FastDiv::make((unsigned)a.nblk);
+  // chunks per staged row: 16-byte copies, or element-sized copies when rows are not 16-byte multiples
+  const int chb = (a.chunk == 16) ? 16 : se;
+  a.fd_cpr = FastDiv::make((unsigned)std::max(1, segb / chb));
+  size_t smem = 2 * (size_t)a.raw_bytes + (size_t)a.lpc * a.ldm * cs + (size_t)a.fp.M * cs;
+  return launch_lines_impl(a, dfm, 1, io_in, io_out, p->threads_y, smem, 0, st);
 }
 
 cudaError_t launch_zsolve(const pp_plan* p, void* data, int transpose, cudaStream_t st) {
@@ -449,6 +520,11 @@ cudaError_t launch_zsolve(const pp_plan* p, void* data, int transpose, cudaStrea
   a.nz = p->nz;
   a.cplx = (p->layout != 2);
   a.nreal = p->splane;
+  // rows of the spectral plane: padded row length (reals) and the reals that carry modes
+  if (p->layout == 1) { a.row_reals = 2 * p->nx; a.row_valid = 2 * p->nx; a.row_modes = p->nx; }
+  else if (p->layout == 0) { a.row_reals = (int)p->xrow; a.row_valid = p->nx + 2; a.row_modes = p->nx / 2 + 1; }
+  else { a.row_reals = (int)p->xrow; a.row_valid = p->nx; a.row_modes = p->nx; }
+  a.fd_row = FastDiv::make((unsigned)a.row_reals);
   a.modes = p->d_modes;
   a.wtab = p->d_wtab;
   a.qtab = p->d_qtab;
@@ -482,6 +558,36 @@ static pp_status run_pipeline(pp_plan* p, const void* f, void* u, int transpose,
   return PP_OK;
 }
 
+// ------------------------------------------------------------------ batched solves as one graph
+// A batch (plans[i]: f[i] -> u[i]) is captured once into a CUDA graph -- the five launches of
+// every member -- and replayed with a single cudaGraphLaunch while the same plans and pointers
+// come back.  Destroying a plan evicts every cached graph that uses it.
+namespace {
+struct BatchGraph {
+  std::vector<const void*> key;  // plans, then f, then u
+  cudaGraphExec_t exec;
+};
+std::mutex g_batch_mu;
+std::vector<BatchGraph> g_batch_cache;  // most recent last
+constexpr size_t kBatchCacheMax = 8;
+
+void evict_plan(const pp_plan* p) {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  for (size_t i = 0; i < g_batch_cache.size();) {
+    const auto& k = g_batch_cache[i].key;
+    size_t n = k.size() / 3;
+    bool uses = false;
+    for (size_t j = 0; j < n; j++) uses |= (k[j] == p);
+    if (uses) {
+      cudaGraphExecDestroy(g_batch_cache[i].exec);
+      g_batch_cache.erase(g_batch_cache.begin() + i);
+    } else {
+      i++;
+    }
+  }
+}
+}  // namespace
+
 // ------------------------------------------------------------------ C ABI
 extern "C" {
 
@@ -506,12 +612,14 @@ pp_status pp_plan_create(pp_plan** out, int nx, int ny, int nz, const pp_bc bc[6
     if ((bc[2 * a] == PP_BC_PERIODIC) != (bc[2 * a + 1] == PP_BC_PERIODIC))
       return fail(PP_ERR_BC_PAIRING, "axis %d: periodic must be given on both faces", a);
   if (opt)
-    for (int i = 0; i < 8; i++)
+    for (int i = 0; i < 7; i++)
       if (opt->reserved[i]) return fail(PP_ERR_INVALID_ARG, "options.reserved must be zero");
+  const int tmax = (dtype == PP_F64) ? 256 : 512;  // double-float kernels use up to 255 registers
+  if (opt && (opt->staged < 0 || opt->staged > 2)) return fail(PP_ERR_INVALID_ARG, "options.staged must be 0, 1 or 2");
   if (opt && (opt->threads_x < 0 || opt->threads_y < 0 || opt->lines_x < 0 || opt->cols_y < 0 ||
-              (opt->threads_x && (opt->threads_x % 32 || opt->threads_x > 512)) ||
-              (opt->threads_y && (opt->threads_y % 32 || opt->threads_y > 512))))
-    return fail(PP_ERR_INVALID_ARG, "options: thread counts must be multiples of 32, at most 512");
+              (opt->threads_x && (opt->threads_x % 32 || opt->threads_x > tmax)) ||
+              (opt->threads_y && (opt->threads_y % 32 || opt->threads_y > tmax))))
+    return fail(PP_ERR_INVALID_ARG, "options: thread counts must be multiples of 32, at most %d", tmax);
   for (int v : {nx, ny})
     if (v < 2 || v > 4096 || v % 2 || !smooth23(v))
       return fail(PP_ERR_UNSUPPORTED_SIZE, "nx, ny must be even 2^a 3^b in [2, 4096] (got %d x %d)", nx, ny);
@@ -535,7 +643,9 @@ pp_status pp_plan_create(pp_plan** out, int nx, int ny, int nz, const pp_bc bc[6
   for (int i = 0; i < 6; i++)
     if (bc[i] == PP_BC_DIRICHLET) p->singular = false;
   p->elem = (dtype == PP_F64) ? 8 : 4;
-  p->xrow = (p->kx == AX_P) ? (long long)nx + 2 : nx;
+  // x-spectral rows are padded to a multiple of 4 reals (16 bytes of FP32) so every row and
+  // column segment can be staged with 16-byte asynchronous copies
+  p->xrow = (((p->kx == AX_P) ? (long long)nx + 2 : nx) + 3) / 4 * 4;
   p->xplane = p->xrow * ny;
   if (p->layout == 1) p->splane = 2LL * nx * (ny / 2 + 1);
   else p->splane = p->xplane;
@@ -564,6 +674,7 @@ pp_status pp_plan_create(pp_plan** out, int nx, int ny, int nz, const pp_bc bc[6
 pp_status pp_plan_destroy(pp_plan* plan) {
   if (!plan) return PP_OK;
   cudaDeviceSynchronize();
+  evict_plan(plan);
   free_plan(plan);
   return PP_OK;
 }
@@ -615,10 +726,93 @@ pp_status pp_solve_refined(pp_plan* p, const void* f, void* u, pp_stream_t strea
 
 pp_status pp_solve_batched(pp_plan* const* plans, const void* const* f, void* const* u, int n, pp_stream_t stream) {
   if (n < 0 || (n > 0 && (!plans || !f || !u))) return fail(PP_ERR_INVALID_ARG, "bad batch arguments");
-  for (int i = 0; i < n; i++) {
-    pp_status s = pp_solve(plans[i], f[i], u[i], stream);
-    if (s != PP_OK) return s;
+  if (n == 0) return PP_OK;
+  for (int i = 0; i < n; i++)
+    if (!plans[i] || !f[i] || !u[i]) return fail(PP_ERR_INVALID_ARG, "batch member %d: NULL plan or pointer", i);
+  std::vector<const void*> key;
+  key.reserve(3 * (size_t)n);
+  for (int i = 0; i < n; i++) key.push_back(plans[i]);
+  for (int i = 0; i < n; i++) key.push_back(f[i]);
+  for (int i = 0; i < n; i++) key.push_back(u[i]);
+  cudaStream_t st = (cudaStream_t)stream;
+  {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (size_t i = 0; i < g_batch_cache.size(); i++) {
+      if (g_batch_cache[i].key == key) {
+        BatchGraph hit = g_batch_cache[i];
+        g_batch_cache.erase(g_batch_cache.begin() + i);
+        g_batch_cache.push_back(hit);
+        CUDA_OK(cudaGraphLaunch(hit.exec, st));
+        return PP_OK;
+      }
+    }
   }
+  // Capture the batch on private streams: a fork event fans the members out over up to
+  // kBranches capture streams (members that share a plan stay on one branch, in order, since
+  // they share its workspace), a join brings them back; the graph's branches run concurrently.
+  constexpr int kBranches = 8;
+  std::vector<const pp_plan*> uniq;
+  std::vector<int> branch(n);
+  for (int i = 0; i < n; i++) {
+    int b = -1;
+    for (size_t j = 0; j < uniq.size(); j++)
+      if (uniq[j] == plans[i]) { b = (int)(j % kBranches); break; }
+    if (b < 0) { b = (int)(uniq.size() % kBranches); uniq.push_back(plans[i]); }
+    branch[i] = b;
+  }
+  const int nb = (int)std::min<size_t>(uniq.size(), kBranches);
+  cudaStream_t cap;
+  CUDA_OK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  std::vector<cudaStream_t> br(nb, nullptr);
+  std::vector<cudaEvent_t> ev(nb + 1, nullptr);
+  cudaError_t e = cudaSuccess;
+  for (int b = 0; b < nb && e == cudaSuccess; b++) e = cudaStreamCreateWithFlags(&br[b], cudaStreamNonBlocking);
+  for (int b = 0; b <= nb && e == cudaSuccess; b++) e = cudaEventCreateWithFlags(&ev[b], cudaEventDisableTiming);
+  auto cleanup = [&]() {
+    for (cudaStream_t x : br) if (x) cudaStreamDestroy(x);
+    for (cudaEvent_t x : ev) if (x) cudaEventDestroy(x);
+    cudaStreamDestroy(cap);
+  };
+  if (e != cudaSuccess) { cleanup(); return fail(PP_ERR_CUDA, "batch streams/events: %s", cudaGetErrorString(e)); }
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) {
+    cleanup();
+    return fail(PP_ERR_CUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
+  }
+  pp_status s = PP_OK;
+  e = cudaEventRecord(ev[nb], cap);
+  for (int b = 0; b < nb && e == cudaSuccess; b++) e = cudaStreamWaitEvent(br[b], ev[nb], 0);
+  if (e != cudaSuccess) s = fail(PP_ERR_CUDA, "batch fork: %s", cudaGetErrorString(e));
+  for (int i = 0; i < n && s == PP_OK; i++) s = run_pipeline(plans[i], f[i], u[i], 0, br[branch[i]]);
+  for (int b = 0; b < nb; b++) {
+    cudaEventRecord(ev[b], br[b]);
+    cudaStreamWaitEvent(cap, ev[b], 0);
+  }
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(cap, &graph);
+  cleanup();
+  if (s != PP_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (e != cudaSuccess) return fail(PP_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(PP_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+  e = cudaGraphLaunch(exec, st);
+  if (e != cudaSuccess) {
+    cudaGraphExecDestroy(exec);
+    return fail(PP_ERR_CUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
+  }
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  if (g_batch_cache.size() >= kBatchCacheMax) {
+    // the evicted graph may still be running on some stream: destroy it only after it finished
+    cudaStreamSynchronize(st);
+    cudaGraphExecDestroy(g_batch_cache.front().exec);
+    g_batch_cache.erase(g_batch_cache.begin());
+  }
+  g_batch_cache.push_back(BatchGraph{std::move(key), exec});
   return PP_OK;
 }
 

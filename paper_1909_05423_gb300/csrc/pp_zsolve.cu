@@ -49,7 +49,11 @@ template <class S>
 __global__ void __launch_bounds__(256) k_zsolve(const ZArgs a) {
   long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= a.nreal) return;
-  const long long mi = a.cplx ? (s >> 1) : s;
+  // slot s of the (padded) spectral plane -> row, column; padding columns carry no mode
+  const unsigned row = a.fd_row.div((unsigned)s);
+  const int col = (int)(s - (long long)row * a.row_reals);
+  if (col >= a.row_valid) return;
+  const long long mi = (long long)row * a.row_modes + (a.cplx ? (col >> 1) : col);
   const ZMode m = a.modes[mi];
   S* base = reinterpret_cast<S*>(a.data) + s;
   const long long P = a.plane;

@@ -143,3 +143,48 @@ def test_batched_uneven(oracle):
         assert rel_l2(o.cpu().numpy(), r) <= TOL_F64
     for p in plans:
         p.close()
+
+
+def test_batched_graph_replay_and_shared_plan(oracle):
+    """The batch is one cached CUDA graph: a second call with the same lists replays it (new data in
+    the same buffers), a member that reuses a plan shares its workspace and still comes out right."""
+    import paper_1909_05423_gb300 as pp
+    shapes = [((8, 12, 18), "PPNNDD"), ((6, 18, 12), "DNPPNN"), ((10, 6, 24), "NNNNNN")]
+    plans = [pp.Plan(s, bc, (1.0, 1.0, 1.0), "f64") for s, bc in shapes]
+    plans.append(plans[0])  # the same plan twice: one branch, in order
+    shapes.append(shapes[0])
+    fs = [torch.empty(s, dtype=torch.float64, device="cuda") for s, _ in shapes]
+    us = [torch.empty_like(f) for f in fs]
+    for rep in range(2):
+        host = [workloads.uniform_source(s, seed=300 + 10 * rep + i) for i, (s, _) in enumerate(shapes)]
+        for f, h in zip(fs, host):
+            f.copy_(torch.from_numpy(h))
+        pp.solve_batched(plans, fs, us)
+        torch.cuda.synchronize()
+        for (s, bc), h, u in zip(shapes, host, us):
+            assert rel_l2(u.cpu().numpy(), oracle.solve(h, bc)) <= TOL_F64
+    for p in plans[:3]:
+        p.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "mixed_f32io"])
+def test_batched_config4_shaped(oracle, dtype):
+    """Config-4 shaped batch (sides drawn per axis, boundary sets drawn per axis/face), scaled down
+    to sides {12..48} so the oracle stays fast; 24 grids in one graph launch."""
+    import paper_1909_05423_gb300 as pp
+    grids = [g for g in workloads.batched_grids(seed=4, count=24, sides=(12, 18, 24, 32, 36, 48))]
+    io = torch.float32 if dtype == "mixed_f32io" else torch.float64
+    plans, fs, refs = [], [], []
+    for i, (shape, bc) in enumerate(grids):
+        f = workloads.uniform_source(shape, seed=500 + i)
+        plans.append(pp.Plan(shape, bc, (1.0 / shape[2], 1.0 / shape[1], 1.0 / shape[0]), dtype))
+        fs.append(torch.from_numpy(f).to(device="cuda", dtype=io))
+        refs.append(oracle.solve(f.astype(np.float32).astype(np.float64) if dtype == "mixed_f32io" else f, bc,
+                                 (1.0 / shape[2], 1.0 / shape[1], 1.0 / shape[0])))
+    outs = pp.solve_batched(plans, fs)
+    torch.cuda.synchronize()
+    tol = TOL_F64 if dtype == "f64" else 1e-6
+    for o, r in zip(outs, refs):
+        assert rel_l2(o.double().cpu().numpy(), r) <= tol
+    for p in plans:
+        p.close()
