@@ -72,9 +72,7 @@ typedef struct pp_plan_options {
   int threads_y;   /* CTA size of the y-line kernels (0 = automatic) */
   int lines_x;     /* lines per CTA, x kernels (0 = automatic) */
   int cols_y;      /* columns per CTA, y kernels (0 = automatic) */
-  int staged;      /* line kernels: 0 = automatic, 1 = one tile per CTA with direct loads,
-                      2 = persistent CTAs with cp.async-staged tiles */
-  int reserved[7]; /* must be zero */
+  int reserved[8]; /* must be zero */
 } pp_plan_options;
 
 typedef struct pp_plan pp_plan;

@@ -174,4 +174,55 @@ __device__ __forceinline__ void fft_lines(cx<R>* buf, int nlines, int ldm, const
   }
 }
 
+// ---------------------------------------------------------------- compile-time length
+// For a power-of-two length MC known at compile time the stage sequence (radix 8 while it
+// divides, then 4, then 2) and every index division are resolved by the compiler.
+template <int REM> struct CtRadix { static constexpr int v = (REM % 8 == 0) ? 8 : (REM % 4 == 0 ? 4 : 2); };
+
+template <class R, int RAD, bool INV, int MC, int S>
+__device__ __forceinline__ void fft_stage_ct(cx<R>* buf, int nlines, int ldm, const cx<R>* tw) {
+  constexpr int NB = NBut<RAD>::v;
+  constexpr int nbl = MC / RAD;
+  const int total = nlines * nbl;
+  cx<R> a[NB][RAD];
+#pragma unroll
+  for (int i = 0; i < NB; i++) {
+    int b = threadIdx.x + i * blockDim.x;
+    if (b < total) {
+      int line = b / nbl, j = b % nbl;
+      const cx<R>* x = buf + line * ldm + j;
+#pragma unroll
+      for (int u = 0; u < RAD; u++) a[i][u] = x[u * nbl];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NB; i++) {
+    int b = threadIdx.x + i * blockDim.x;
+    if (b < total) {
+      int line = b / nbl, j = b % nbl;
+      int p = j / S, q = j % S;
+      dft_r<R, RAD, INV>(a[i]);
+      cx<R>* y = buf + line * ldm + q + S * RAD * p;
+      y[0] = a[i][0];
+      const int ps = p * S;
+#pragma unroll
+      for (int t = 1; t < RAD; t++) {
+        cx<R> w = tw[ps * t];
+        y[S * t] = INV ? cmulc(a[i][t], w) : cmul(a[i][t], w);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <class R, bool INV, int MC, int S>
+__device__ __forceinline__ void fft_lines_ct(cx<R>* buf, int nlines, int ldm, const cx<R>* tw) {
+  if constexpr (S < MC) {
+    constexpr int RAD = CtRadix<MC / S>::v;
+    fft_stage_ct<R, RAD, INV, MC, S>(buf, nlines, ldm, tw);
+    fft_lines_ct<R, INV, MC, S * RAD>(buf, nlines, ldm, tw);
+  }
+}
+
 }  // namespace pp

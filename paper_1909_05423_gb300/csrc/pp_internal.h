@@ -43,12 +43,7 @@ struct LineArgs {
   int in_line, in_pos;          // input: stride between consecutive lines / positions (reals)
   long long out_line, out_pos;  // output: stride between consecutive lines / positions (reals)
   int ntiles;         // tiles of the launch (x: lpc rows; y: one plane x tx columns)
-  int raw_bytes;      // bytes of one staging buffer (a raw input tile)
-  int chunk;          // 16: 16-byte asynchronous copies; 0: element-sized copies
-  int staged;         // 1: persistent CTAs with cp.async-staged tiles; 0: one tile per CTA, direct loads
   int tx, ncols, nblk;  // y: columns per tile, columns per plane, column blocks per plane
-  int in_rows;        // y: positions staged per column
-  int raw_row;        // y: staged row length (reals)
   const void* tw;     // stage twiddles w_M^j, j < M (complex, arithmetic type)
   const void* aux;    // pre/post twiddles (complex, arithmetic type), layout per kind
   FftPlan fp;
@@ -58,7 +53,6 @@ struct LineArgs {
   FastDiv fd_lpp;     // lines per plane
   FastDiv fd_parts;   // 1 or 2
   FastDiv fd_nblk;    // column blocks per plane
-  FastDiv fd_cpr;     // 16-byte chunks per staged row
 };
 constexpr int kMaxLpc = 512;  // lines per CTA (bounded so the per-line bases fit in shared memory)
 
@@ -123,7 +117,6 @@ struct pp_plan {
   // launch shapes
   int threads_x, lpc_x, ldm_x;
   int threads_y, lpc_y, ldm_y;
-  int staged;           // line-kernel variant (see LineArgs::staged)
   // mixed-precision refinement scratch
   void* d_resid;       // residual / correction (FP64 I/O size)
   void* d_mean;        // kMeanParts partial sums + 1 mean (float2 each), singular refinement

@@ -1,0 +1,344 @@
+// pp_lines.cuh -- batched line transforms along x (contiguous lines) and y (strided columns).
+//
+// Every transform of the paper's table of forward/backward transforms is computed through a
+// complex FFT with pre- and post-processing (Sec. "Boundary Conditions": pre-processing,
+// complex Fourier transform, post-processing):
+//   * real DFT of length N (periodic): the even/odd samples packed as one complex line of
+//     length M = N/2, FFT, then the Hermitian split X_k = E_k + w_N^k O_k;
+//   * DCT-II ("DCT10", Neumann): Makhoul's reordering (even samples in order, odd samples
+//     reversed), a real DFT, and the twiddle exp(-i pi k / 2N), real part; the values of
+//     index N-k come from the same complex number (minus its imaginary part);
+//   * DST-II ("DST10", Dirichlet): DCT-II of the sign-alternated line, output reversed;
+//   * their inverses DCT-III / DST-III ("DCT01"/"DST01") by the reverse steps;
+//   * DCT-IV / DST-IV (one Dirichlet and one Neumann face) via a length-N/2 complex FFT with
+//     pre-twiddle exp(-i pi (4n+1)/4N) and post-twiddle exp(-i pi k/N).
+// All inverse transforms are unnormalised syntheses; the constant inverse weights (1/N, or
+// 2/N for type IV) are applied once, in the tridiagonal solve.
+//
+// One CTA transforms `lpc` lines in shared memory: x lines are `lpc` consecutive rows, y lines
+// are `tx` adjacent columns of one plane (times 2 when the real and imaginary parts of complex
+// columns are transformed as separate real lines).  Pre-processing reads global memory (x:
+// consecutive threads along a line; y: consecutive threads across columns, so every access is
+// a coalesced row segment), the FFT runs in place in shared memory, post-processing writes
+// global memory in the same patterns.  The kernels are templated on the complex FFT length MC
+// (MC = 0: read from the plan at run time; MC = a power of two: the stage sequence and all
+// index divisions are compile-time).
+#pragma once
+#include <algorithm>
+#include <type_traits>
+
+#include "pp_internal.h"
+
+namespace pp {
+
+// base offsets (in reals) of global line g of the launch
+__device__ __forceinline__ long long line_base(const LineArgs& a, unsigned g, bool out) {
+  unsigned plane = a.fd_lpp.div(g);
+  unsigned r = g - plane * (unsigned)a.lines_per_plane;
+  unsigned c = a.fd_parts.div(r), part = r - c * (unsigned)a.parts;
+  return out ? (long long)plane * a.out_plane + (long long)c * a.out_line + part
+             : (long long)plane * a.in_plane + (long long)c * a.in_line + part;
+}
+
+// Visit every (line L, item k) of the tile.  x: k fastest (consecutive threads along a line);
+// y: L fastest (consecutive threads across columns).  KC: compile-time item count (0: fdk).
+template <bool OY, int KC, class F>
+__device__ __forceinline__ void for_items(const LineArgs& a, int nl, const FastDiv& fdk, F&& fn) {
+  const int K = KC ? KC : (int)fdk.d;
+  const int tot = (OY ? a.lpc : nl) * K;
+#pragma unroll 4
+  for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+    int L, k;
+    if (OY) {
+      unsigned q = a.fd_lpc.div((unsigned)t);
+      L = t - (int)(q * a.fd_lpc.d);
+      k = (int)q;
+      if (L >= nl) continue;
+    } else {
+      if constexpr (KC > 0) {
+        L = t / KC;
+        k = t % KC;
+      } else {
+        unsigned q = fdk.div((unsigned)t);
+        L = (int)q;
+        k = t - (int)q * K;
+      }
+    }
+    fn(L, k);
+  }
+}
+
+template <class R, class SI> struct SrcGlobal {
+  const SI* in;
+  const long long* bases;  // per-line bases (shared memory)
+  long long pos;
+  __device__ __forceinline__ long long base(int L) const { return bases[L]; }
+  __device__ __forceinline__ R ld(long long b, int j) const { return Io<R, SI>::ld(in, b + (long long)j * pos); }
+};
+
+// Pre-processing of one tile: builds the complex FFT input of every line in `buf`.  The kind is
+// uniform, so each kind has its own loop; unrolling lets every thread keep several loads in flight.
+template <class R, bool OY, int MC, class Src>
+__device__ __noinline__ void pre_tile(const LineArgs& a, const Src src, int nl, cx<R>* buf) {
+  const int M = MC ? MC : a.fp.M;
+  const int N = a.N, ldm = a.ldm, kind = a.kind;
+  const cx<R>* aux = reinterpret_cast<const cx<R>*>(a.aux);
+  auto ldr = [&](auto b, int j) -> R { return src.ld(b, j); };
+  auto ldc = [&](auto b, int j) -> cx<R> { return cx<R>{src.ld(b, j), src.ld(b + 1, j)}; };
+  const FastDiv& fk = a.fd_kpre;
+  switch (kind) {
+    case LK_R2C:
+      for_items<OY, MC>(a, nl, fk, [&](int L, int k) {
+        auto b = src.base(L);
+        buf[L * ldm + k] = cx<R>{ldr(b, 2 * k), ldr(b, 2 * k + 1)};
+      });
+      break;
+    case LK_DCT2:
+    case LK_DST2: {
+      // v_j = u_{2j} (j < M), u_{2N-1-2j} (j >= M); DST-II alternates the sign of odd samples
+      const bool dst = (kind == LK_DST2);
+      for_items<OY, MC>(a, nl, fk, [&](int L, int k) {
+        auto b = src.base(L);
+        int j0 = 2 * k, j1 = 2 * k + 1;
+        int s0 = j0 < M ? 2 * j0 : 2 * N - 1 - 2 * j0;
+        int s1 = j1 < M ? 2 * j1 : 2 * N - 1 - 2 * j1;
+        R v0 = ldr(b, s0), v1 = ldr(b, s1);
+        if (dst) {
+          if (j0 >= M) v0 = Ar<R>::neg(v0);
+          if (j1 >= M) v1 = Ar<R>::neg(v1);
+        }
+        buf[L * ldm + k] = cx<R>{v0, v1};
+      });
+      break;
+    }
+    case LK_DCT4:
+    case LK_DST4: {
+      const bool c4 = (kind == LK_DCT4);
+      for_items<OY, MC>(a, nl, fk, [&](int L, int k) {
+        auto b = src.base(L);
+        R e = ldr(b, 2 * k), o = ldr(b, N - 1 - 2 * k);
+        cx<R> z = c4 ? cx<R>{e, o} : cx<R>{o, e};
+        buf[L * ldm + k] = cmul(z, aux[k]);  // exp(-i pi (4k+1) / 4N)
+      });
+      break;
+    }
+    case LK_C2C_F:
+    case LK_C2C_I:
+      for_items<OY, MC>(a, nl, fk, [&](int L, int k) { buf[L * ldm + k] = ldc(src.base(L), k); });
+      break;
+    case LK_C2R:
+    case LK_DCT3:
+    case LK_DST3: {
+      // Hermitian pair (X_k, X_{M-k}) -> Z_k = E + i O, E = X_k + conj X_{M-k},
+      // O = (X_k - conj X_{M-k}) exp(+2 pi i k / N); imaginary parts of X_0, X_M dropped.
+      // DCT-III/DST-III first form V_j = exp(+i pi j / 2N) (Y_j - i Y_{N-j}), Y_N = 0
+      // (DST-III reads Y reversed).
+      const cx<R>* w4 = aux + (M + 1);
+      for_items<OY, MC>(a, nl, fk, [&](int L, int k) {
+        auto b = src.base(L);
+        cx<R> Xk, Xm;
+        if (kind == LK_C2R) {
+          Xk = ldc(b, k);
+          Xm = ldc(b, M - k);
+        } else {
+          auto Y = [&](int j) -> R {
+            if (j >= N) return Ar<R>::zero();
+            return ldr(b, kind == LK_DCT3 ? j : N - 1 - j);
+          };
+          cx<R> t0{Y(k), Ar<R>::neg(Y(N - k))};
+          cx<R> t1{Y(M - k), Ar<R>::neg(Y(M + k))};
+          Xk = cmulc(t0, w4[k]);
+          Xm = cmulc(t1, w4[M - k]);
+        }
+        if (k == 0) { Xk.im = Ar<R>::zero(); Xm.im = Ar<R>::zero(); }
+        cx<R> Xc = cconj(Xm);
+        cx<R> E = cadd(Xk, Xc);
+        cx<R> O = cmulc(csub(Xk, Xc), aux[k]);  // * conj(w_N^k)
+        buf[L * ldm + k] = cx<R>{Ar<R>::sub(E.re, O.im), Ar<R>::add(E.im, O.re)};
+      });
+      break;
+    }
+    default: break;
+  }
+}
+
+// Post-processing of one transformed tile: extracts the wanted transform from `buf` and writes
+// it to global memory (line bases in s_bout).  One loop per (uniform) kind, as in pre_tile.
+template <class R, class SO, bool OY, int MC>
+__device__ __noinline__ void post_tile(const LineArgs& a, const cx<R>* buf, int nl, const long long* s_bout) {
+  const int M = MC ? MC : a.fp.M;
+  const int N = a.N, ldm = a.ldm, kind = a.kind;
+  const cx<R>* aux = reinterpret_cast<const cx<R>*>(a.aux);
+  SO* out = reinterpret_cast<SO*>(a.out);
+  const long long op = a.out_pos;
+  auto str = [&](long long b, int j, R v) { Io<R, SO>::st(out, b + (long long)j * op, v); };
+  auto stc = [&](long long b, int j, cx<R> v) {
+    long long o = b + (long long)j * op;
+    Io<R, SO>::st(out, o, v.re);
+    Io<R, SO>::st(out, o + 1, v.im);
+  };
+  const FastDiv& fk = a.fd_kpost;
+  switch (kind) {
+    case LK_R2C:
+    case LK_DCT2:
+    case LK_DST2: {
+      // X_k = E_k + w_N^k O_k from the Hermitian pair (Z_k, Z_{M-k}); DCT-II: W = exp(-i pi k/2N) X_k,
+      // Y_k = Re W, Y_{N-k} = -Im W; DST-II writes the DCT-II of the sign-alternated line reversed.
+      for_items<OY, 0>(a, nl, fk, [&](int L, int k) {
+        const long long b = s_bout[L];
+        const cx<R>* zl = buf + L * ldm;
+        cx<R> Zk = zl[k == M ? 0 : k];
+        cx<R> Zm = zl[k == 0 ? 0 : M - k];
+        cx<R> Zc = cconj(Zm);
+        cx<R> E = chalf(cadd(Zk, Zc));
+        cx<R> dd = csub(Zk, Zc);
+        cx<R> O = chalf(cx<R>{dd.im, Ar<R>::neg(dd.re)});  // (Zk - conj Zm) / (2i)
+        cx<R> X = cadd(E, cmul(O, aux[k]));               // + w_N^k O
+        if (kind == LK_R2C) { stc(b, k, X); return; }
+        cx<R> W = cmul(X, aux[M + 1 + k]);                 // exp(-i pi k / 2N)
+        int i0 = k, i1 = N - k;
+        if (kind == LK_DST2) { i0 = N - 1 - k; i1 = k - 1; }
+        str(b, i0, W.re);
+        if (k >= 1 && k < M) str(b, i1, Ar<R>::neg(W.im));
+      });
+      break;
+    }
+    case LK_DCT4:
+    case LK_DST4: {
+      const bool c4 = (kind == LK_DCT4);
+      for_items<OY, MC>(a, nl, fk, [&](int L, int k) {
+        const long long b = s_bout[L];
+        cx<R> s = cmul(buf[L * ldm + k], aux[M + k]);  // exp(-i pi k / N)
+        str(b, 2 * k, s.re);
+        str(b, N - 1 - 2 * k, c4 ? Ar<R>::neg(s.im) : s.im);
+      });
+      break;
+    }
+    case LK_C2C_F:
+    case LK_C2C_I:
+      for_items<OY, MC>(a, nl, fk, [&](int L, int k) { stc(s_bout[L], k, buf[L * ldm + k]); });
+      break;
+    case LK_C2R:
+      for_items<OY, MC>(a, nl, fk, [&](int L, int k) {
+        const long long b = s_bout[L];
+        cx<R> z = buf[L * ldm + k];
+        str(b, 2 * k, z.re);
+        str(b, 2 * k + 1, z.im);
+      });
+      break;
+    case LK_DCT3:
+    case LK_DST3: {
+      // u_{sigma(j)} = v_j with sigma the Makhoul order (DST-III: signs alternate)
+      const bool dst = (kind == LK_DST3);
+      for_items<OY, MC>(a, nl, fk, [&](int L, int k) {
+        const long long b = s_bout[L];
+        cx<R> z = buf[L * ldm + k];
+        int j0 = 2 * k, j1 = 2 * k + 1;
+        int s0 = j0 < M ? 2 * j0 : 2 * N - 1 - 2 * j0;
+        int s1 = j1 < M ? 2 * j1 : 2 * N - 1 - 2 * j1;
+        R v0 = z.re, v1 = z.im;
+        if (dst) {
+          if (j0 >= M) v0 = Ar<R>::neg(v0);
+          if (j1 >= M) v1 = Ar<R>::neg(v1);
+        }
+        str(b, s0, v0);
+        str(b, s1, v1);
+      });
+      break;
+    }
+    default: break;
+  }
+}
+
+// One tile per CTA (x: lpc consecutive rows; y: one plane x tx columns).
+template <class R, class SI, class SO, bool OY, int MC>
+__global__ void __launch_bounds__(512, 1) k_lines(const LineArgs args) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ long long s_bin[kMaxLpc], s_bout[kMaxLpc];
+  const LineArgs& a = args;
+  const int M = MC ? MC : a.fp.M;
+  const int ldm = a.ldm;
+  cx<R>* buf = reinterpret_cast<cx<R>*>(smem_raw);
+  cx<R>* tws = buf + (size_t)a.lpc * ldm;
+  const cx<R>* twg = reinterpret_cast<const cx<R>*>(a.tw);
+  for (int i = threadIdx.x; i < M; i += blockDim.x) tws[i] = twg[i];
+  const int kind = a.kind;
+  const bool inv = (kind == LK_C2R || kind == LK_C2C_I || kind == LK_DCT3 || kind == LK_DST3);
+  int line0, nl;
+  if (!OY) {
+    line0 = (int)blockIdx.x * a.lpc;
+    nl = min(a.lpc, a.nlines - line0);
+  } else {
+    const int plane = (int)a.fd_nblk.div(blockIdx.x);
+    const int blk = (int)blockIdx.x - plane * a.nblk;
+    const int c0 = blk * a.tx;
+    line0 = plane * a.lines_per_plane + c0 * a.parts;
+    nl = min(a.tx, a.ncols - c0) * a.parts;
+  }
+  for (int L = threadIdx.x; L < nl; L += blockDim.x) {
+    s_bin[L] = line_base(a, (unsigned)(line0 + L), false);
+    s_bout[L] = line_base(a, (unsigned)(line0 + L), true);
+  }
+  __syncthreads();
+  pre_tile<R, OY, MC>(a, SrcGlobal<R, SI>{reinterpret_cast<const SI*>(a.in), s_bin, (long long)a.in_pos}, nl, buf);
+  __syncthreads();
+  if constexpr (MC > 0) {
+    if (inv) fft_lines_ct<R, true, MC, 1>(buf, nl, ldm, tws);
+    else fft_lines_ct<R, false, MC, 1>(buf, nl, ldm, tws);
+  } else {
+    if (inv) fft_lines<R, true>(buf, nl, ldm, a.fp, tws);
+    else fft_lines<R, false>(buf, nl, ldm, a.fp, tws);
+    if (a.fp.nst == 0) __syncthreads();
+  }
+  post_tile<R, SO, OY, MC>(a, buf, nl, s_bout);
+}
+
+template <class R, class SI, class SO, bool OY, int MC>
+cudaError_t launch_lines_k(const LineArgs& a, int threads, cudaStream_t st) {
+  auto k = k_lines<R, SI, SO, OY, MC>;
+  // dynamic shared memory above 48 KB must be opted into; plans keep it <= 200 KB
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const size_t sm = ((size_t)a.lpc * a.ldm + (size_t)a.fp.M) * sizeof(cx<R>);
+  k<<<a.ntiles, threads, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
+// storage codes of the launchers
+enum { ST_F64 = 0, ST_F32 = 1, ST_SPILL = 2 };
+
+// Pick the instantiation for (orientation, input/output storage) and the FFT length.
+template <class R, class SP, int MC>
+cudaError_t dispatch_io(const LineArgs& a, int oy, int sin, int sout, int threads, cudaStream_t st) {
+  if (oy) {
+    if (sin == ST_SPILL && sout == ST_SPILL) return launch_lines_k<R, SP, SP, true, MC>(a, threads, st);
+    return cudaErrorInvalidValue;
+  }
+  if (sin == ST_F64 && sout == ST_SPILL) return launch_lines_k<R, double, SP, false, MC>(a, threads, st);
+  if (sin == ST_SPILL && sout == ST_F64) return launch_lines_k<R, SP, double, false, MC>(a, threads, st);
+  if (sin == ST_SPILL && sout == ST_SPILL) return launch_lines_k<R, SP, SP, false, MC>(a, threads, st);
+  if (std::is_same<R, float>::value) {
+    // FP32 I/O: the spill type is float as well
+    if ((sin == ST_F32 && sout == ST_SPILL) || (sin == ST_SPILL && sout == ST_F32))
+      return launch_lines_k<R, SP, SP, false, MC>(a, threads, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Instantiation groups (one translation unit each, compiled in parallel): compile-time lengths
+// {64, 128, 256} and {512, 1024}, plus the run-time-length kernels.  Each returns
+// cudaErrorNotSupported when the length is not in its group.
+#define PP_LINES_GROUP_DECL(name) \
+  cudaError_t name(const LineArgs& a, int oy, int sin, int sout, int threads, cudaStream_t st)
+PP_LINES_GROUP_DECL(lines_df_small);
+PP_LINES_GROUP_DECL(lines_df_large);
+PP_LINES_GROUP_DECL(lines_df_any);
+PP_LINES_GROUP_DECL(lines_f32_small);
+PP_LINES_GROUP_DECL(lines_f32_large);
+PP_LINES_GROUP_DECL(lines_f32_any);
+
+}  // namespace pp

@@ -336,14 +336,10 @@ static void free_plan(pp_plan* p) {
 }
 
 // launch shapes: threads per CTA and lines per CTA of the x and y line kernels.  Shared memory
-// per CTA = 2 staging buffers (raw tiles) + the complex work buffer + the stage twiddles.
-static size_t round16(size_t b) { return (b + 15) & ~(size_t)15; }
-
+// per CTA = the complex work buffer + the stage twiddles.
 static void choose_shapes(pp_plan* p, const pp_plan_options* opt) {
-  p->staged = (opt && opt->staged == 2) ? 1 : 0;
   size_t cs = (p->dtype == PP_F64) ? 16 : 8;          // bytes per complex in shared memory
   size_t se = p->elem;                                  // bytes per spill real
-  size_t ioe = (p->dtype == PP_MIXED_F32IO) ? 4 : 8;    // bytes per I/O real
   const size_t smem_cap = 200 * 1024;
   // x lines: a staged tile holds lpc rows of the wider of (grid row, spectral row)
   {
@@ -358,8 +354,7 @@ static void choose_shapes(pp_plan* p, const pp_plan_options* opt) {
     lpc = std::min(lpc, kMaxLpc);
     lpc = std::min(lpc, nlines);
     int ldm = M + 1;
-    size_t rowb = std::max((size_t)p->nx * ioe, (size_t)p->xrow * se);
-    auto need = [&](int l) { return 2 * round16((size_t)l * rowb) + (size_t)l * ldm * cs + (size_t)M * cs; };
+    auto need = [&](int l) { return (size_t)l * ldm * cs + (size_t)M * cs; };
     while (lpc > 1 && need(lpc) > smem_cap) lpc--;
     p->threads_x = T;
     p->lpc_x = lpc;
@@ -387,12 +382,7 @@ static void choose_shapes(pp_plan* p, const pp_plan_options* opt) {
     cols = std::min(cols, kMaxLpc / parts);
     cols = std::min(cols, ncols);
     int ldm = M + 1;
-    // staged rows: the spectral columns of layout 1 are complex (2 reals) on the inverse side
-    size_t colr = (cplx_cols || p->layout == 1) ? 2 : 1;
-    auto need = [&](int c) {
-      return 2 * round16((size_t)p->ny * round16((size_t)c * colr * se)) + (size_t)c * parts * ldm * cs +
-             (size_t)M * cs;
-    };
+    auto need = [&](int c) { return (size_t)c * parts * ldm * cs + (size_t)M * cs; };
     while (cols > 1 && need(cols) > smem_cap) cols--;
     p->threads_y = T;
     p->lpc_y = cols * parts;
@@ -427,11 +417,7 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
   a.in = in;
   a.out = out;
   const bool dfm = (p->dtype == PP_F64);
-  const size_t cs = dfm ? 16 : 8;
-  const int se = (int)p->elem;
-  const int ioe = (p->dtype == PP_MIXED_F32IO) ? 4 : 8;
   const long long nxy = (long long)p->nx * p->ny;
-  const bool in_aligned = ((uintptr_t)in % 16) == 0;
   if (axis == 0) {
     bool per = (p->kx == AX_P);
     a.N = p->nx;
@@ -446,24 +432,16 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
     a.aux = p->d_aux_x;
     long long grid_plane = nxy, grid_row = p->nx;
     long long sp_plane = p->xplane, sp_row = p->xrow;
-    int ies;  // bytes per input real
     if (dir == 0) {
       a.in_plane = grid_plane; a.in_line = (int)grid_row; a.in_pos = 1;
       a.out_plane = sp_plane; a.out_line = sp_row; a.out_pos = per ? 2 : 1;
-      ies = (io_in == ST_SPILL) ? se : ioe;
     } else {
       a.in_plane = sp_plane; a.in_line = (int)sp_row; a.in_pos = per ? 2 : 1;
       a.out_plane = grid_plane; a.out_line = grid_row; a.out_pos = 1;
-      ies = se;
     }
     a.ntiles = (a.nlines + a.lpc - 1) / a.lpc;
-    a.raw_bytes = (int)round16((size_t)a.lpc * a.in_line * ies);
-    a.chunk = (in_aligned && ((size_t)a.in_line * ies) % 16 == 0) ? 16 : 0;
-    a.in_rows = 0;
-    a.staged = p->staged;
     finish_args(a);
-    size_t smem = 2 * (size_t)a.raw_bytes + (size_t)a.lpc * a.ldm * cs + (size_t)a.fp.M * cs;
-    return launch_lines_impl(a, dfm, 0, io_in, io_out, p->threads_x, smem, 0, st);
+    return launch_lines_impl(a, dfm, 0, io_in, io_out, p->threads_x, 0, 0, st);
   }
   // y
   const bool cplx_cols = (p->layout == 0);
@@ -496,20 +474,9 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
   a.ncols = ncols;
   a.nblk = (ncols + a.tx - 1) / a.tx;
   a.ntiles = a.nblk * p->nz;
-  a.in_rows = (a.kind == LK_C2R) ? a.fp.M + 1 : p->ny;
-  int segb = a.tx * a.in_line * se;
-  a.raw_row = (int)(round16((size_t)segb) / se);
-  a.raw_bytes = (int)round16((size_t)a.in_rows * a.raw_row * se);
-  a.chunk = (in_aligned && segb % 16 == 0 && ((size_t)a.in_pos * se) % 16 == 0 && ((size_t)a.in_plane * se) % 16 == 0)
-                ? 16 : 0;
-  a.staged = p->staged;
   finish_args(a);
   a.fd_nblk = FastDiv::make((unsigned)a.nblk);
-  // chunks per staged row: 16-byte copies, or element-sized copies when rows are not 16-byte multiples
-  const int chb = (a.chunk == 16) ? 16 : se;
-  a.fd_cpr = FastDiv::make((unsigned)std::max(1, segb / chb));
-  size_t smem = 2 * (size_t)a.raw_bytes + (size_t)a.lpc * a.ldm * cs + (size_t)a.fp.M * cs;
-  return launch_lines_impl(a, dfm, 1, io_in, io_out, p->threads_y, smem, 0, st);
+  return launch_lines_impl(a, dfm, 1, io_in, io_out, p->threads_y, 0, 0, st);
 }
 
 cudaError_t launch_zsolve(const pp_plan* p, void* data, int transpose, cudaStream_t st) {
@@ -612,10 +579,9 @@ pp_status pp_plan_create(pp_plan** out, int nx, int ny, int nz, const pp_bc bc[6
     if ((bc[2 * a] == PP_BC_PERIODIC) != (bc[2 * a + 1] == PP_BC_PERIODIC))
       return fail(PP_ERR_BC_PAIRING, "axis %d: periodic must be given on both faces", a);
   if (opt)
-    for (int i = 0; i < 7; i++)
+    for (int i = 0; i < 8; i++)
       if (opt->reserved[i]) return fail(PP_ERR_INVALID_ARG, "options.reserved must be zero");
   const int tmax = (dtype == PP_F64) ? 256 : 512;  // double-float kernels use up to 255 registers
-  if (opt && (opt->staged < 0 || opt->staged > 2)) return fail(PP_ERR_INVALID_ARG, "options.staged must be 0, 1 or 2");
   if (opt && (opt->threads_x < 0 || opt->threads_y < 0 || opt->lines_x < 0 || opt->cols_y < 0 ||
               (opt->threads_x && (opt->threads_x % 32 || opt->threads_x > tmax)) ||
               (opt->threads_y && (opt->threads_y % 32 || opt->threads_y > tmax))))
@@ -643,8 +609,7 @@ pp_status pp_plan_create(pp_plan** out, int nx, int ny, int nz, const pp_bc bc[6
   for (int i = 0; i < 6; i++)
     if (bc[i] == PP_BC_DIRICHLET) p->singular = false;
   p->elem = (dtype == PP_F64) ? 8 : 4;
-  // x-spectral rows are padded to a multiple of 4 reals (16 bytes of FP32) so every row and
-  // column segment can be staged with 16-byte asynchronous copies
+  // x-spectral rows are padded to a multiple of 4 reals so every row starts 16-byte aligned
   p->xrow = (((p->kx == AX_P) ? (long long)nx + 2 : nx) + 3) / 4 * 4;
   p->xplane = p->xrow * ny;
   if (p->layout == 1) p->splane = 2LL * nx * (ny / 2 + 1);
