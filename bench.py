@@ -41,6 +41,21 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def replica_aggregate(ms_local: float, points_local: int, dist=None, device="cpu"):
+    """Whole-job figures of independent replicas: the slowest rank's time per step (max over
+    ranks) and the total points of all ranks per that time (Gpoints/s).  No data is exchanged,
+    only these two scalars."""
+    import torch
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms_local, points_local / (ms_local * 1e-3) / 1e9
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    p = torch.tensor([float(points_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    ms = t.item()
+    return ms, p.item() / (ms * 1e-3) / 1e9
+
+
 def _dist():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -140,6 +155,114 @@ def run_reference(args):
     return 0
 
 
+def _events_ms(fn, reps, warmup=2):
+    import torch
+    st = torch.cuda.current_stream()
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        fn()
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _config3(pp, workloads, args):
+    """512^3 mixed precision (FP32 transforms, double-float z, one FP64 refinement step), all-periodic
+    and all-Neumann manufactured cos/sin products; errors against the exact discrete solution (which the
+    FP64 oracle reproduces to roundoff) and the FP64 path; rates with and without refinement."""
+    import math
+
+    import numpy as np
+    import torch
+    n = args.n3
+    sp = (1.0 / n,) * 3
+    out = {}
+    cases = {
+        "PPPPPP": [(1.0, ("cos", 2 * math.pi), ("cos", 2 * math.pi), ("cos", 2 * math.pi)),
+                   (0.5, ("sin", 4 * math.pi), ("sin", 2 * math.pi), ("cos", 6 * math.pi))],
+        "NNNNNN": [(1.0, ("cos", math.pi), ("cos", 3 * math.pi), ("cos", 6 * math.pi)),
+                   (0.5, ("cos", 2 * math.pi), ("cos", math.pi), ("cos", 2 * math.pi))],
+    }
+    h = 1.0 / n
+    lam = lambda k: (2.0 * math.cos(k * h) - 2.0) / (h * h)
+    for bc, terms in cases.items():
+        u_star, f = workloads.manufactured((n, n, n), sp, terms)
+        # exact discrete solution: each product term is a discrete eigenvector
+        u_dis = np.zeros_like(u_star)
+        for amp, (fx, kx), (fy, ky), (fz, kz) in terms:
+            t, _ = workloads.manufactured((n, n, n), sp, [(amp, (fx, kx), (fy, ky), (fz, kz))])
+            u_dis += t * (-(kx * kx + ky * ky + kz * kz) / (lam(kx) + lam(ky) + lam(kz)))
+        u_dis -= u_dis.mean()
+        ft = torch.from_numpy(f).cuda()
+        ref = torch.from_numpy(u_dis).cuda()
+        p64 = pp.Plan((n, n, n), bc, sp, "f64")
+        pm = pp.Plan((n, n, n), bc, sp, "mixed_f64io")
+        u64, um, ur = torch.empty_like(ft), torch.empty_like(ft), torch.empty_like(ft)
+        t64 = _events_ms(lambda: p64.solve(ft, u64), args.steps)
+        tm = _events_ms(lambda: pm.solve(ft, um), args.steps)
+        tr = _events_ms(lambda: pm.solve_refined(ft, ur), args.steps)
+        nrm = torch.linalg.vector_norm(ref).item()
+        rel = lambda x: torch.linalg.vector_norm(x - ref).item() / nrm
+        out[bc] = {"n": n, "f64_ms": t64, "mixed_ms": tm, "refined_ms": tr,
+                   "f64_gpoints_s": n ** 3 / t64 / 1e6, "mixed_gpoints_s": n ** 3 / tm / 1e6,
+                   "refined_gpoints_s": n ** 3 / tr / 1e6, "mixed_speedup_vs_f64": t64 / tm,
+                   "rel_l2_vs_exact_discrete": {"f64": rel(u64), "mixed": rel(um), "refined": rel(ur)}}
+        p64.close()
+        pm.close()
+        del ft, ref, u64, um, ur
+        torch.cuda.empty_cache()
+    return out
+
+
+def _config4(pp, workloads, args):
+    """64 independent grids, sides drawn from {32,...,256} per axis and boundary conditions per axis/face,
+    U[-1,1] sources; one graph launch per batch (FP64 and FP32 I/O)."""
+    import torch
+    grids = workloads.batched_grids(seed=4, count=64)
+    pts = sum(s[0] * s[1] * s[2] for s, _ in grids)
+    out = {"grids": 64, "points": pts}
+    g = torch.Generator(device="cuda")
+    g.manual_seed(4)
+    for dtype, tdt in (("f64", torch.float64), ("mixed_f32io", torch.float32)):
+        plans = [pp.Plan(s, bc, (1.0 / s[2], 1.0 / s[1], 1.0 / s[0]), dtype) for s, bc in grids]
+        fs = [torch.empty(s, dtype=tdt, device="cuda").uniform_(-1.0, 1.0, generator=g) for s, _ in grids]
+        us = [torch.empty_like(x) for x in fs]
+        ms = _events_ms(lambda: pp.solve_batched(plans, fs, us), args.steps)
+        out[dtype] = {"ms_per_batch": ms, "gpoints_s": pts / ms / 1e6, "graph_launches_per_batch": 1}
+        for p in plans:
+            p.close()
+        del fs, us
+        torch.cuda.empty_cache()
+    return out
+
+
+def _config5(pp, workloads, args):
+    """256^3 FP64, periodic x/y, Dirichlet z; f = 16 Gaussian blobs; L = 0.5||S f - u_t||^2:
+    forward solve + adjoint solve (the gradient dL/df) through the autograd Function."""
+    import numpy as np
+    import torch
+    n = 256
+    sp = (1.0 / n,) * 3
+    amp, centre, width = workloads.gaussian_blobs((n, n, n), sp, seed=5, count=16)
+    f = torch.from_numpy(workloads.blob_field((n, n, n), sp, amp, centre, width)).cuda().requires_grad_(True)
+    ut = torch.from_numpy(np.random.default_rng(6).uniform(-1, 1, size=(n, n, n))).cuda()
+    plan = pp.Plan((n, n, n), "PPPPDD", sp, "f64")
+
+    def step():
+        f.grad = None
+        uu = pp.PoissonSolve.apply(f, plan)
+        loss = 0.5 * ((uu - ut) ** 2).sum()
+        loss.backward()
+
+    ms = _events_ms(step, args.steps)
+    plan.close()
+    return {"n": n, "ms_forward_plus_adjoint": ms, "gpoints_s_forward_plus_adjoint": n ** 3 / ms / 1e6}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -201,13 +324,8 @@ def run_ours(args):
     clocks.start()
     ms, per = timed(plan, f, u, args.steps, args.warmup)
     clk = clocks.stop()
-    ms_all = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_all = t.item()
+    ms_all, value = replica_aggregate(ms, npts, dist, device="cuda")
     plan.status()
-    value = world * npts / (ms_all * 1e-3) / 1e9
 
     # roofline of the dominant kernel: algorithmic bytes = read input once + write output once
     elem = 8  # FP64 I/O and double-float spill: 8 bytes per real
@@ -234,6 +352,16 @@ def run_ours(args):
                                    "rel_l2_vs_f64_path": err_m}
         pm.close()
         del um
+
+    # ---------------------------------------------------------------- config 3: mixed precision on MMS
+    if not args.no_variants:
+        del u
+        torch.cuda.empty_cache()
+        variants["config3_mixed_mms"] = _config3(pp, workloads, args)
+        variants["config4_batched"] = _config4(pp, workloads, args)
+        variants["config5_adjoint"] = _config5(pp, workloads, args)
+        u = torch.empty_like(f)
+        plan.solve(f, u)
 
     # ---------------------------------------------------------------- end to end through host buffers
     e2e = None
@@ -296,6 +424,8 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--n3", type=int, default=512, help="grid side of the config-3 mixed-precision variant")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

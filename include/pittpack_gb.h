@@ -72,7 +72,10 @@ typedef struct pp_plan_options {
   int threads_y;   /* CTA size of the y-line kernels (0 = automatic) */
   int lines_x;     /* lines per CTA, x kernels (0 = automatic) */
   int cols_y;      /* columns per CTA, y kernels (0 = automatic) */
-  int reserved[8]; /* must be zero */
+  int autotune;    /* 1: time candidate CTA sizes / lines per CTA for the x and y kernels at plan
+                      creation and keep the fastest (results cached per device, sizes, boundary
+                      set and dtype for the life of the process); 0: fixed heuristics */
+  int reserved[7]; /* must be zero */
 } pp_plan_options;
 
 typedef struct pp_plan pp_plan;

@@ -43,6 +43,7 @@ struct LineArgs {
   int in_line, in_pos;          // input: stride between consecutive lines / positions (reals)
   long long out_line, out_pos;  // output: stride between consecutive lines / positions (reals)
   int ntiles;         // tiles of the launch (x: lpc rows; y: one plane x tx columns)
+  int vec_ok;         // x lines: both arrays 32-byte aligned (vectorised pre/post allowed)
   int tx, ncols, nblk;  // y: columns per tile, columns per plane, column blocks per plane
   const void* tw;     // stage twiddles w_M^j, j < M (complex, arithmetic type)
   const void* aux;    // pre/post twiddles (complex, arithmetic type), layout per kind

@@ -68,7 +68,48 @@ __device__ __forceinline__ void for_items(const LineArgs& a, int nl, const FastD
   }
 }
 
+// Vector access to 2 or 4 consecutive reals at a real offset that is a multiple of 2 / 4
+// (rows of x tiles are 16-byte aligned; the host checks the array pointers).
+template <class R, class S> struct Vec;
+template <> struct Vec<df, double> {
+  __device__ static __forceinline__ void ld2(const double* p, long long o, df* v) {
+    double2 a = __ldg(reinterpret_cast<const double2*>(p + o));
+    v[0] = df_from_double(a.x); v[1] = df_from_double(a.y);
+  }
+  __device__ static __forceinline__ void st2(double* p, long long o, const df* v) {
+    *reinterpret_cast<double2*>(p + o) = make_double2(df_to_double(v[0]), df_to_double(v[1]));
+  }
+};
+template <> struct Vec<df, float2> {
+  __device__ static __forceinline__ void ld2(const float2* p, long long o, df* v) {
+    float4 a = __ldg(reinterpret_cast<const float4*>(p + o));
+    v[0] = df{a.x, a.y}; v[1] = df{a.z, a.w};
+  }
+  __device__ static __forceinline__ void st2(float2* p, long long o, const df* v) {
+    *reinterpret_cast<float4*>(p + o) = make_float4(v[0].hi, v[0].lo, v[1].hi, v[1].lo);
+  }
+};
+template <> struct Vec<float, double> {
+  __device__ static __forceinline__ void ld2(const double* p, long long o, float* v) {
+    double2 a = __ldg(reinterpret_cast<const double2*>(p + o));
+    v[0] = f32_from_double(a.x); v[1] = f32_from_double(a.y);
+  }
+  __device__ static __forceinline__ void st2(double* p, long long o, const float* v) {
+    *reinterpret_cast<double2*>(p + o) = make_double2(double_from_f32(v[0]), double_from_f32(v[1]));
+  }
+};
+template <> struct Vec<float, float> {
+  __device__ static __forceinline__ void ld2(const float* p, long long o, float* v) {
+    float2 a = __ldg(reinterpret_cast<const float2*>(p + o));
+    v[0] = a.x; v[1] = a.y;
+  }
+  __device__ static __forceinline__ void st2(float* p, long long o, const float* v) {
+    *reinterpret_cast<float2*>(p + o) = make_float2(v[0], v[1]);
+  }
+};
+
 template <class R, class SI> struct SrcGlobal {
+  using elem_t = SI;
   const SI* in;
   const long long* bases;  // per-line bases (shared memory)
   long long pos;
@@ -86,6 +127,48 @@ __device__ __noinline__ void pre_tile(const LineArgs& a, const Src src, int nl, 
   auto ldr = [&](auto b, int j) -> R { return src.ld(b, j); };
   auto ldc = [&](auto b, int j) -> cx<R> { return cx<R>{src.ld(b, j), src.ld(b + 1, j)}; };
   const FastDiv& fk = a.fd_kpre;
+  if constexpr (!OY && MC > 0 && std::is_same<Src, SrcGlobal<R, typename Src::elem_t>>::value) {
+    // x lines of a compile-time length: every thread reads runs of consecutive samples
+    using SI = typename Src::elem_t;
+    if (a.vec_ok) {
+      if (kind == LK_DCT2 || kind == LK_DST2) {
+        // u[4k..4k+3] -> z_k = (u_4k, u_4k+2), z_{M-1-k} = (u_4k+3, u_4k+1) (negated for DST-II)
+        const bool dst = (kind == LK_DST2);
+        for_items<false, MC / 2>(a, nl, fk, [&](int L, int k) {
+          const long long b = src.base(L) + 4LL * k;
+          R v[4];
+          Vec<R, SI>::ld2(src.in, b, v);
+          Vec<R, SI>::ld2(src.in, b + 2, v + 2);
+          buf[L * ldm + k] = cx<R>{v[0], v[2]};
+          buf[L * ldm + (M - 1 - k)] = dst ? cx<R>{Ar<R>::neg(v[3]), Ar<R>::neg(v[1])} : cx<R>{v[3], v[1]};
+        });
+        return;
+      }
+      if (kind == LK_DCT4 || kind == LK_DST4) {
+        // u[2n], u[2n+1] and u[N-2-2n], u[N-1-2n] -> z_n and z_{M-1-n}
+        const bool c4 = (kind == LK_DCT4);
+        for_items<false, MC / 2>(a, nl, fk, [&](int L, int n) {
+          const long long b = src.base(L);
+          R lo[2], hi[2];
+          Vec<R, SI>::ld2(src.in, b + 2 * n, lo);
+          Vec<R, SI>::ld2(src.in, b + (N - 2 - 2 * n), hi);
+          cx<R> z0 = c4 ? cx<R>{lo[0], hi[1]} : cx<R>{hi[1], lo[0]};
+          cx<R> z1 = c4 ? cx<R>{hi[0], lo[1]} : cx<R>{lo[1], hi[0]};
+          buf[L * ldm + n] = cmul(z0, aux[n]);
+          buf[L * ldm + (M - 1 - n)] = cmul(z1, aux[M - 1 - n]);
+        });
+        return;
+      }
+      if (kind == LK_R2C) {
+        for_items<false, MC>(a, nl, fk, [&](int L, int k) {
+          R v[2];
+          Vec<R, SI>::ld2(src.in, src.base(L) + 2 * k, v);
+          buf[L * ldm + k] = cx<R>{v[0], v[1]};
+        });
+        return;
+      }
+    }
+  }
   switch (kind) {
     case LK_R2C:
       for_items<OY, MC>(a, nl, fk, [&](int L, int k) {
@@ -178,6 +261,46 @@ __device__ __noinline__ void post_tile(const LineArgs& a, const cx<R>* buf, int 
     Io<R, SO>::st(out, o + 1, v.im);
   };
   const FastDiv& fk = a.fd_kpost;
+  if constexpr (!OY && MC > 0) {
+    if (a.vec_ok) {
+      if (kind == LK_DCT3 || kind == LK_DST3) {
+        // u[4k..4k+3] = (z_k.re, s z_{M-1-k}.im, z_k.im, s z_{M-1-k}.re), s = -1 for DST-III
+        const bool dst = (kind == LK_DST3);
+        for_items<false, MC / 2>(a, nl, fk, [&](int L, int k) {
+          const long long b = s_bout[L] + 4LL * k;
+          cx<R> z0 = buf[L * ldm + k], z1 = buf[L * ldm + (M - 1 - k)];
+          if (dst) z1 = cx<R>{Ar<R>::neg(z1.re), Ar<R>::neg(z1.im)};
+          R v[4] = {z0.re, z1.im, z0.im, z1.re};
+          Vec<R, SO>::st2(out, b, v);
+          Vec<R, SO>::st2(out, b + 2, v + 2);
+        });
+        return;
+      }
+      if (kind == LK_DCT4 || kind == LK_DST4) {
+        // Y_2k = s_k.re, Y_{N-1-2k} = -+s_k.im; the partner k' = M-1-k fills Y_{2k+1}, Y_{N-2-2k}
+        const bool c4 = (kind == LK_DCT4);
+        for_items<false, MC / 2>(a, nl, fk, [&](int L, int k) {
+          const long long b = s_bout[L];
+          const int k1 = M - 1 - k;
+          cx<R> s0 = cmul(buf[L * ldm + k], aux[M + k]);
+          cx<R> s1 = cmul(buf[L * ldm + k1], aux[M + k1]);
+          R i0 = c4 ? Ar<R>::neg(s0.im) : s0.im, i1 = c4 ? Ar<R>::neg(s1.im) : s1.im;
+          R lo[2] = {s0.re, i1}, hi[2] = {s1.re, i0};
+          Vec<R, SO>::st2(out, b + 2 * k, lo);
+          Vec<R, SO>::st2(out, b + (N - 2 - 2 * k), hi);
+        });
+        return;
+      }
+      if (kind == LK_C2R) {
+        for_items<false, MC>(a, nl, fk, [&](int L, int k) {
+          cx<R> z = buf[L * ldm + k];
+          R v[2] = {z.re, z.im};
+          Vec<R, SO>::st2(out, s_bout[L] + 2 * k, v);
+        });
+        return;
+      }
+    }
+  }
   switch (kind) {
     case LK_R2C:
     case LK_DCT2:

@@ -371,7 +371,7 @@ static void choose_shapes(pp_plan* p, const pp_plan_options* opt) {
     size_t col_bytes = (cplx_cols ? 2 : 1) * se;
     // CTA size: 128 threads unless that leaves column segments below one 32-byte sector
     int T = 128;
-    const int tmax = (p->dtype == PP_F64) ? 256 : 512;
+    const int tmax = 512;
     if (opt && opt->threads_y) T = opt->threads_y;
     else
       while (T < tmax && (size_t)std::max(1, (kCapPerThread3 * T / std::max(M, 1)) / parts) * col_bytes < 32) T *= 2;
@@ -440,6 +440,7 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
       a.out_plane = grid_plane; a.out_line = grid_row; a.out_pos = 1;
     }
     a.ntiles = (a.nlines + a.lpc - 1) / a.lpc;
+    a.vec_ok = (((uintptr_t)in | (uintptr_t)out) % 32 == 0) ? 1 : 0;
     finish_args(a);
     return launch_lines_impl(a, dfm, 0, io_in, io_out, p->threads_x, 0, 0, st);
   }
@@ -525,6 +526,118 @@ static pp_status run_pipeline(pp_plan* p, const void* f, void* u, int transpose,
   return PP_OK;
 }
 
+// ------------------------------------------------------------------ autotuner
+// Times candidate launch shapes of the x kernels (x-forward + x-inverse) and of the y kernels
+// (y-forward + y-inverse) on scratch grids and keeps the fastest.  Results are cached per
+// (device, sizes, boundary set, dtype) for the life of the process.
+namespace {
+struct TuneEnt {
+  int dev, nx, ny, nz, dtype, bc[6];
+  pp_plan_options best;
+};
+std::mutex g_tune_mu;
+std::vector<TuneEnt> g_tune_cache;
+}  // namespace
+
+static pp_status autotune(pp_plan* p) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const TuneEnt& e : g_tune_cache)
+      if (e.dev == dev && e.nx == p->nx && e.ny == p->ny && e.nz == p->nz && e.dtype == p->dtype &&
+          memcmp(e.bc, p->bc, sizeof e.bc) == 0) {
+        choose_shapes(p, &e.best);
+        return PP_OK;
+      }
+  }
+  const size_t io = (p->dtype == PP_MIXED_F32IO) ? 4 : 8;
+  const size_t bytes = (size_t)p->nx * p->ny * p->nz * io;
+  void *f = nullptr, *u = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t ce = cudaMalloc(&f, bytes);
+  if (ce == cudaSuccess) ce = cudaMalloc(&u, bytes);
+  if (ce == cudaSuccess) ce = cudaMemset(f, 0, bytes);
+  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  auto cleanup = [&]() {
+    if (f) cudaFree(f);
+    if (u) cudaFree(u);
+    if (st) cudaStreamDestroy(st);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  if (ce != cudaSuccess) { cleanup(); return fail(PP_ERR_OUT_OF_MEMORY, "autotune scratch: %s", cudaGetErrorString(ce)); }
+  // time stages s0, s1 (3 runs after one warm-up), in ms; +inf on a failed launch
+  auto time_pair = [&](int s0, int s1) -> float {
+    float best = 1e30f;
+    for (int r = 0; r < 4; r++) {
+      cudaEventRecord(e0, st);
+      if (run_stage(p, s0, f, u, 0, st) != PP_OK || run_stage(p, s1, f, u, 0, st) != PP_OK) return 1e30f;
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) return 1e30f;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (r > 0) best = std::min(best, ms);
+    }
+    return best;
+  };
+  const int tmax = 512;
+  const int tcand[] = {64, 128, 256, 512};
+  pp_plan_options best;
+  memset(&best, 0, sizeof best);
+  // x kernels
+  float bx = 1e30f;
+  for (int T : tcand) {
+    if (T > tmax) continue;
+    for (int half = 0; half < 2; half++) {
+      pp_plan_options o;
+      memset(&o, 0, sizeof o);
+      o.threads_x = T;
+      choose_shapes(p, &o);
+      if (half) {
+        if (p->lpc_x < 2) continue;
+        o.lines_x = p->lpc_x / 2;
+        choose_shapes(p, &o);
+      }
+      float t = time_pair(0, 4);
+      if (t < bx) { bx = t; best.threads_x = o.threads_x; best.lines_x = o.lines_x; }
+    }
+  }
+  // y kernels (x part fixed at its best)
+  float by = 1e30f;
+  for (int T : tcand) {
+    if (T > tmax) continue;
+    for (int half = 0; half < 2; half++) {
+      pp_plan_options o = best;
+      o.threads_y = T;
+      o.cols_y = 0;
+      choose_shapes(p, &o);
+      if (half) {
+        int parts = (p->layout == 0 && p->ky != AX_P) ? 2 : 1;
+        int cols = p->lpc_y / parts;
+        if (cols < 2) continue;
+        o.cols_y = cols / 2;
+        choose_shapes(p, &o);
+      }
+      float t = time_pair(1, 3);
+      if (t < by) { by = t; best.threads_y = o.threads_y; best.cols_y = o.cols_y; }
+    }
+  }
+  cleanup();
+  if (bx >= 1e30f || by >= 1e30f) return fail(PP_ERR_CUDA, "autotune: no candidate launch shape ran");
+  choose_shapes(p, &best);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  TuneEnt ent;
+  ent.dev = dev; ent.nx = p->nx; ent.ny = p->ny; ent.nz = p->nz; ent.dtype = p->dtype;
+  memcpy(ent.bc, p->bc, sizeof ent.bc);
+  ent.best = best;
+  g_tune_cache.push_back(ent);
+  return PP_OK;
+}
+
 // ------------------------------------------------------------------ batched solves as one graph
 // A batch (plans[i]: f[i] -> u[i]) is captured once into a CUDA graph -- the five launches of
 // every member -- and replayed with a single cudaGraphLaunch while the same plans and pointers
@@ -579,9 +692,9 @@ pp_status pp_plan_create(pp_plan** out, int nx, int ny, int nz, const pp_bc bc[6
     if ((bc[2 * a] == PP_BC_PERIODIC) != (bc[2 * a + 1] == PP_BC_PERIODIC))
       return fail(PP_ERR_BC_PAIRING, "axis %d: periodic must be given on both faces", a);
   if (opt)
-    for (int i = 0; i < 8; i++)
+    for (int i = 0; i < 7; i++)
       if (opt->reserved[i]) return fail(PP_ERR_INVALID_ARG, "options.reserved must be zero");
-  const int tmax = (dtype == PP_F64) ? 256 : 512;  // double-float kernels use up to 255 registers
+  const int tmax = 512;
   if (opt && (opt->threads_x < 0 || opt->threads_y < 0 || opt->lines_x < 0 || opt->cols_y < 0 ||
               (opt->threads_x && (opt->threads_x % 32 || opt->threads_x > tmax)) ||
               (opt->threads_y && (opt->threads_y % 32 || opt->threads_y > tmax))))
@@ -632,6 +745,10 @@ pp_status pp_plan_create(pp_plan** out, int nx, int ny, int nz, const pp_bc bc[6
                 cudaGetErrorString(e));
   }
   cudaMemset(p->d_status, 0, sizeof(int));
+  if (opt && opt->autotune) {
+    pp_status ts = autotune(p);
+    if (ts != PP_OK) { free_plan(p); return ts; }
+  }
   *out = p;
   return PP_OK;
 }

@@ -1,0 +1,95 @@
+"""Full-size checks in the launch configuration bench.py times: a 1024^3 grid, Neumann x /
+Dirichlet y / Neumann z, FP64 in/out.  The oracle cannot solve 1024^3 in test time, so the
+checks are properties that hold at any size, evaluated on sampled outputs:
+
+* a manufactured eigenfunction product is returned as the exact discrete solution
+  u* * (-sum k^2 / sum lambda_d) (closed form), compared element by element at sampled cells;
+* for a random source, the oracle's 7-point stencil at sampled cells reproduces f.  The bound
+  is set by the arithmetic: a relative rounding error e in u becomes a residual of about
+  sqrt(42)/h^2 * e * |u| (the stencil's weight norm), which at h = 1/1024 and e ~ 1e-14
+  (double-float) is ~1e-9 |f|; the test allows 2e-8 (rms) and 2e-7 (max), while any error in
+  the method (eigenvalues, transforms, end rows) gives O(1);
+* the mixed-precision path stays within 1e-6 relative L2 of the FP64 path.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from tests import helpers
+from tests.gpu_common import need_gpu, torch
+
+pytestmark = pytest.mark.gpu
+N = 1024
+BC = "NNDDNN"
+
+
+@pytest.fixture(scope="module")
+def plan64():
+    need_gpu()
+    import paper_1909_05423_gb300 as pp
+    free, _ = torch.cuda.mem_get_info()
+    if free < 48 << 30:
+        pytest.skip("needs ~48 GB of free device memory")
+    p = pp.Plan((N, N, N), BC, (1.0 / N,) * 3, "f64")
+    yield p
+    p.close()
+
+
+def _cells(seed, count=200000):
+    rng = np.random.default_rng(seed)
+    idx = rng.integers(0, N ** 3, size=count, dtype=np.int64)
+    # include the six faces' extreme cells
+    faces = [0, N - 1]
+    extra = [k * N * N + j * N + i for k in faces for j in faces for i in faces]
+    return np.concatenate([idx, np.array(extra, dtype=np.int64)])
+
+
+def test_fullsize_exact_eigenfunction(plan64):
+    h = 1.0 / N
+    kap = [math.pi, 2 * math.pi, 3 * math.pi]  # cos(pi x) sin(2 pi y) cos(3 pi z) fits Neumann-x/Dirichlet-y/Neumann-z
+    c = (torch.arange(N, device="cuda", dtype=torch.float64) + 0.5) * h
+    fx, fy, fz = torch.cos(kap[0] * c), torch.sin(kap[1] * c), torch.cos(kap[2] * c)
+    u_star = fz[:, None, None] * fy[None, :, None] * fx[None, None, :]
+    f = -(sum(k * k for k in kap)) * u_star
+    u = plan64.solve(f)
+    torch.cuda.synchronize()
+    plan64.status()
+    ratio = helpers.discrete_solution_ratio(kap, [h] * 3)
+    idx = torch.from_numpy(_cells(1)).cuda()
+    got = u.flatten()[idx].cpu().numpy()
+    want = (u_star.flatten()[idx] * ratio).cpu().numpy()
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want)) * 10
+    rel = torch.linalg.vector_norm(u - u_star * ratio).item() / torch.linalg.vector_norm(u_star * ratio).item()
+    assert rel <= 1e-12
+
+
+def test_fullsize_residual_sampled(plan64, oracle):
+    g = torch.Generator(device="cuda")
+    g.manual_seed(2)
+    f = torch.empty((N, N, N), dtype=torch.float64, device="cuda").uniform_(-1.0, 1.0, generator=g)
+    f -= f.mean()
+    u = plan64.solve(f)
+    torch.cuda.synchronize()
+    idx = _cells(3)
+    u_host = u.cpu().numpy()
+    lap = oracle.laplacian_at(u_host, BC, (1.0 / N,) * 3, idx)
+    fs = f.flatten()[torch.from_numpy(idx).cuda()].cpu().numpy()
+    frms = math.sqrt(torch.mean(f * f).item())
+    assert np.max(np.abs(lap - fs)) / frms < 2e-7
+    assert np.sqrt(np.mean((lap - fs) ** 2)) / frms < 2e-8
+
+
+def test_fullsize_mixed_vs_f64(plan64):
+    import paper_1909_05423_gb300 as pp
+    g = torch.Generator(device="cuda")
+    g.manual_seed(2)
+    f = torch.empty((N, N, N), dtype=torch.float64, device="cuda").uniform_(-1.0, 1.0, generator=g)
+    f -= f.mean()
+    u64 = plan64.solve(f)
+    pm = pp.Plan((N, N, N), BC, (1.0 / N,) * 3, "mixed_f64io")
+    um = pm.solve(f)
+    torch.cuda.synchronize()
+    rel = (torch.linalg.vector_norm(um - u64) / torch.linalg.vector_norm(u64)).item()
+    pm.close()
+    assert rel <= 1e-6

@@ -188,3 +188,15 @@ def test_batched_config4_shaped(oracle, dtype):
         assert rel_l2(o.double().cpu().numpy(), r) <= tol
     for p in plans:
         p.close()
+
+
+def test_autotuned_plan_matches_oracle(oracle):
+    """A plan created with autotune=1 (launch shapes timed and chosen at creation, then cached)
+    gives the same parity as the default shapes."""
+    shape = (20, 36, 64)
+    sp = (1.0 / 64, 1.0 / 36, 1.0 / 20)
+    f = workloads.uniform_source(shape, seed=21)
+    ref = oracle.solve(f, "NDPPDD", sp)
+    for _ in range(2):  # second creation hits the cache
+        u = gpu_solve(f, "NDPPDD", sp, options={"autotune": 1})
+        assert rel_l2(u, ref) <= TOL_F64
