@@ -56,6 +56,32 @@ def replica_aggregate(ms_local: float, points_local: int, dist=None, device="cpu
     return ms, p.item() / (ms * 1e-3) / 1e9
 
 
+def _source_hash():
+    """Hash of the kernel sources (the traffic figures in profiles/ are valid only for these)."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1909_05423_gb300", "csrc", "*"))):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(f, "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(stage: str, n: int):
+    """DRAM bytes per launch of `stage` from the committed ncu summary, scaled to n^3, or None when
+    the summary is missing, for another workload, or for kernels that have changed since."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic_solve_f64.json")) as fh:
+            d = json.load(fh)
+    except Exception:
+        return None
+    if d.get("source_hash") != _source_hash() or d.get("bc") != BC:
+        return None
+    v = d.get("per_launch_bytes_at_1024", {}).get(stage)
+    return None if v is None else v * (n / 1024.0) ** 3
+
+
 def _dist():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -398,7 +424,7 @@ def run_ours(args):
                        "stage_ms": dict(zip(STAGES, per)), "path_hbm_gbs_32B_per_point": path_gbs,
                        "path_hbm_frac_32B_per_point": path_gbs / peak},
             "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                         "frac": achieved / peak, "peak_source": peak_kind, "traffic": _traffic(dname, n),
                          "alg_bytes_per_launch": alg_bytes[dname]},
             "variants": variants,
             "cpu_baseline": cpu,
