@@ -373,9 +373,13 @@ __device__ __noinline__ void post_tile(const LineArgs& a, const cx<R>* buf, int 
   }
 }
 
+// Residency target: FP32 kernels aim at two 512-thread CTAs per SM (<= 64 registers), the
+// double-float ones at one (<= 128 registers, their butterflies need them).
+template <class R> struct MinBlocks { static constexpr int v = std::is_same<R, float>::value ? 2 : 1; };
+
 // One tile per CTA (x: lpc consecutive rows; y: one plane x tx columns).
 template <class R, class SI, class SO, bool OY, int MC>
-__global__ void __launch_bounds__(512, 1) k_lines(const LineArgs args) {
+__global__ void __launch_bounds__(512, MinBlocks<R>::v) k_lines(const LineArgs args) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ long long s_bin[kMaxLpc], s_bout[kMaxLpc];
   const LineArgs& a = args;
