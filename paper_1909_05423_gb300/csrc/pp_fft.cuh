@@ -16,6 +16,10 @@ namespace pp {
 
 constexpr int kMaxStages = 16;
 
+// Shared-memory position of element i of a line: one padding slot after every 32 elements, so
+// the strided writes of the early Stockham stages (stride radix x 8..16 bytes) hit distinct banks.
+__device__ __forceinline__ int pad(int i) { return i + (i >> 5); }
+
 // Unsigned division by a run-time invariant divisor with one multiply-high and two shifts
 // (Granlund & Montgomery, "Division by invariant integers using multiplication", 1994):
 // l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1, q = (t + ((n - t) >> min(l,1))) >> max(l-1,0)
@@ -127,9 +131,9 @@ __device__ __forceinline__ void fft_stage(cx<R>* buf, int nlines, int ldm, int s
     if (b < total) {
       int line = (int)fd_nbl.div((unsigned)b), j = b - line * nbl;
       lj[i] = line * ldm + j;
-      const cx<R>* x = buf + line * ldm + j;
+      const cx<R>* x = buf + line * ldm;
 #pragma unroll
-      for (int u = 0; u < RAD; u++) a[i][u] = x[u * nbl];
+      for (int u = 0; u < RAD; u++) a[i][u] = x[pad(j + u * nbl)];
     }
   }
   __syncthreads();
@@ -140,13 +144,14 @@ __device__ __forceinline__ void fft_stage(cx<R>* buf, int nlines, int ldm, int s
       int line = (int)fd_nbl.div((unsigned)b), j = b - line * nbl;
       int p = (int)fd_s.div((unsigned)j), q = j - p * s;
       dft_r<R, RAD, INV>(a[i]);
-      cx<R>* y = buf + line * ldm + q + s * RAD * p;
-      y[0] = a[i][0];
+      cx<R>* y = buf + line * ldm;
+      const int o = q + s * RAD * p;
+      y[pad(o)] = a[i][0];
       const int ps = p * s;
 #pragma unroll
       for (int t = 1; t < RAD; t++) {
         cx<R> w = tw[ps * t];
-        y[s * t] = INV ? cmulc(a[i][t], w) : cmul(a[i][t], w);
+        y[pad(o + s * t)] = INV ? cmulc(a[i][t], w) : cmul(a[i][t], w);
       }
     }
   }
@@ -190,9 +195,9 @@ __device__ __forceinline__ void fft_stage_ct(cx<R>* buf, int nlines, int ldm, co
     int b = threadIdx.x + i * blockDim.x;
     if (b < total) {
       int line = b / nbl, j = b % nbl;
-      const cx<R>* x = buf + line * ldm + j;
+      const cx<R>* x = buf + line * ldm;
 #pragma unroll
-      for (int u = 0; u < RAD; u++) a[i][u] = x[u * nbl];
+      for (int u = 0; u < RAD; u++) a[i][u] = x[pad(j + u * nbl)];
     }
   }
   __syncthreads();
@@ -203,13 +208,14 @@ __device__ __forceinline__ void fft_stage_ct(cx<R>* buf, int nlines, int ldm, co
       int line = b / nbl, j = b % nbl;
       int p = j / S, q = j % S;
       dft_r<R, RAD, INV>(a[i]);
-      cx<R>* y = buf + line * ldm + q + S * RAD * p;
-      y[0] = a[i][0];
+      cx<R>* y = buf + line * ldm;
+      const int o = q + S * RAD * p;
+      y[pad(o)] = a[i][0];
       const int ps = p * S;
 #pragma unroll
       for (int t = 1; t < RAD; t++) {
         cx<R> w = tw[ps * t];
-        y[S * t] = INV ? cmulc(a[i][t], w) : cmul(a[i][t], w);
+        y[pad(o + S * t)] = INV ? cmulc(a[i][t], w) : cmul(a[i][t], w);
       }
     }
   }

@@ -139,8 +139,8 @@ __device__ __noinline__ void pre_tile(const LineArgs& a, const Src src, int nl, 
           R v[4];
           Vec<R, SI>::ld2(src.in, b, v);
           Vec<R, SI>::ld2(src.in, b + 2, v + 2);
-          buf[L * ldm + k] = cx<R>{v[0], v[2]};
-          buf[L * ldm + (M - 1 - k)] = dst ? cx<R>{Ar<R>::neg(v[3]), Ar<R>::neg(v[1])} : cx<R>{v[3], v[1]};
+          buf[L * ldm + pad(k)] = cx<R>{v[0], v[2]};
+          buf[L * ldm + pad((M - 1 - k))] = dst ? cx<R>{Ar<R>::neg(v[3]), Ar<R>::neg(v[1])} : cx<R>{v[3], v[1]};
         });
         return;
       }
@@ -154,8 +154,8 @@ __device__ __noinline__ void pre_tile(const LineArgs& a, const Src src, int nl, 
           Vec<R, SI>::ld2(src.in, b + (N - 2 - 2 * n), hi);
           cx<R> z0 = c4 ? cx<R>{lo[0], hi[1]} : cx<R>{hi[1], lo[0]};
           cx<R> z1 = c4 ? cx<R>{hi[0], lo[1]} : cx<R>{lo[1], hi[0]};
-          buf[L * ldm + n] = cmul(z0, aux[n]);
-          buf[L * ldm + (M - 1 - n)] = cmul(z1, aux[M - 1 - n]);
+          buf[L * ldm + pad(n)] = cmul(z0, aux[n]);
+          buf[L * ldm + pad((M - 1 - n))] = cmul(z1, aux[M - 1 - n]);
         });
         return;
       }
@@ -163,7 +163,7 @@ __device__ __noinline__ void pre_tile(const LineArgs& a, const Src src, int nl, 
         for_items<false, MC>(a, nl, fk, [&](int L, int k) {
           R v[2];
           Vec<R, SI>::ld2(src.in, src.base(L) + 2 * k, v);
-          buf[L * ldm + k] = cx<R>{v[0], v[1]};
+          buf[L * ldm + pad(k)] = cx<R>{v[0], v[1]};
         });
         return;
       }
@@ -173,7 +173,7 @@ __device__ __noinline__ void pre_tile(const LineArgs& a, const Src src, int nl, 
     case LK_R2C:
       for_items<OY, MC>(a, nl, fk, [&](int L, int k) {
         auto b = src.base(L);
-        buf[L * ldm + k] = cx<R>{ldr(b, 2 * k), ldr(b, 2 * k + 1)};
+        buf[L * ldm + pad(k)] = cx<R>{ldr(b, 2 * k), ldr(b, 2 * k + 1)};
       });
       break;
     case LK_DCT2:
@@ -190,7 +190,7 @@ __device__ __noinline__ void pre_tile(const LineArgs& a, const Src src, int nl, 
           if (j0 >= M) v0 = Ar<R>::neg(v0);
           if (j1 >= M) v1 = Ar<R>::neg(v1);
         }
-        buf[L * ldm + k] = cx<R>{v0, v1};
+        buf[L * ldm + pad(k)] = cx<R>{v0, v1};
       });
       break;
     }
@@ -201,13 +201,13 @@ __device__ __noinline__ void pre_tile(const LineArgs& a, const Src src, int nl, 
         auto b = src.base(L);
         R e = ldr(b, 2 * k), o = ldr(b, N - 1 - 2 * k);
         cx<R> z = c4 ? cx<R>{e, o} : cx<R>{o, e};
-        buf[L * ldm + k] = cmul(z, aux[k]);  // exp(-i pi (4k+1) / 4N)
+        buf[L * ldm + pad(k)] = cmul(z, aux[k]);  // exp(-i pi (4k+1) / 4N)
       });
       break;
     }
     case LK_C2C_F:
     case LK_C2C_I:
-      for_items<OY, MC>(a, nl, fk, [&](int L, int k) { buf[L * ldm + k] = ldc(src.base(L), k); });
+      for_items<OY, MC>(a, nl, fk, [&](int L, int k) { buf[L * ldm + pad(k)] = ldc(src.base(L), k); });
       break;
     case LK_C2R:
     case LK_DCT3:
@@ -237,7 +237,7 @@ __device__ __noinline__ void pre_tile(const LineArgs& a, const Src src, int nl, 
         cx<R> Xc = cconj(Xm);
         cx<R> E = cadd(Xk, Xc);
         cx<R> O = cmulc(csub(Xk, Xc), aux[k]);  // * conj(w_N^k)
-        buf[L * ldm + k] = cx<R>{Ar<R>::sub(E.re, O.im), Ar<R>::add(E.im, O.re)};
+        buf[L * ldm + pad(k)] = cx<R>{Ar<R>::sub(E.re, O.im), Ar<R>::add(E.im, O.re)};
       });
       break;
     }
@@ -268,7 +268,7 @@ __device__ __noinline__ void post_tile(const LineArgs& a, const cx<R>* buf, int 
         const bool dst = (kind == LK_DST3);
         for_items<false, MC / 2>(a, nl, fk, [&](int L, int k) {
           const long long b = s_bout[L] + 4LL * k;
-          cx<R> z0 = buf[L * ldm + k], z1 = buf[L * ldm + (M - 1 - k)];
+          cx<R> z0 = buf[L * ldm + pad(k)], z1 = buf[L * ldm + pad((M - 1 - k))];
           if (dst) z1 = cx<R>{Ar<R>::neg(z1.re), Ar<R>::neg(z1.im)};
           R v[4] = {z0.re, z1.im, z0.im, z1.re};
           Vec<R, SO>::st2(out, b, v);
@@ -282,8 +282,8 @@ __device__ __noinline__ void post_tile(const LineArgs& a, const cx<R>* buf, int 
         for_items<false, MC / 2>(a, nl, fk, [&](int L, int k) {
           const long long b = s_bout[L];
           const int k1 = M - 1 - k;
-          cx<R> s0 = cmul(buf[L * ldm + k], aux[M + k]);
-          cx<R> s1 = cmul(buf[L * ldm + k1], aux[M + k1]);
+          cx<R> s0 = cmul(buf[L * ldm + pad(k)], aux[M + k]);
+          cx<R> s1 = cmul(buf[L * ldm + pad(k1)], aux[M + k1]);
           R i0 = c4 ? Ar<R>::neg(s0.im) : s0.im, i1 = c4 ? Ar<R>::neg(s1.im) : s1.im;
           R lo[2] = {s0.re, i1}, hi[2] = {s1.re, i0};
           Vec<R, SO>::st2(out, b + 2 * k, lo);
@@ -293,7 +293,7 @@ __device__ __noinline__ void post_tile(const LineArgs& a, const cx<R>* buf, int 
       }
       if (kind == LK_C2R) {
         for_items<false, MC>(a, nl, fk, [&](int L, int k) {
-          cx<R> z = buf[L * ldm + k];
+          cx<R> z = buf[L * ldm + pad(k)];
           R v[2] = {z.re, z.im};
           Vec<R, SO>::st2(out, s_bout[L] + 2 * k, v);
         });
@@ -310,8 +310,8 @@ __device__ __noinline__ void post_tile(const LineArgs& a, const cx<R>* buf, int 
       for_items<OY, 0>(a, nl, fk, [&](int L, int k) {
         const long long b = s_bout[L];
         const cx<R>* zl = buf + L * ldm;
-        cx<R> Zk = zl[k == M ? 0 : k];
-        cx<R> Zm = zl[k == 0 ? 0 : M - k];
+        cx<R> Zk = zl[pad(k == M ? 0 : k)];
+        cx<R> Zm = zl[pad(k == 0 ? 0 : M - k)];
         cx<R> Zc = cconj(Zm);
         cx<R> E = chalf(cadd(Zk, Zc));
         cx<R> dd = csub(Zk, Zc);
@@ -331,7 +331,7 @@ __device__ __noinline__ void post_tile(const LineArgs& a, const cx<R>* buf, int 
       const bool c4 = (kind == LK_DCT4);
       for_items<OY, MC>(a, nl, fk, [&](int L, int k) {
         const long long b = s_bout[L];
-        cx<R> s = cmul(buf[L * ldm + k], aux[M + k]);  // exp(-i pi k / N)
+        cx<R> s = cmul(buf[L * ldm + pad(k)], aux[M + k]);  // exp(-i pi k / N)
         str(b, 2 * k, s.re);
         str(b, N - 1 - 2 * k, c4 ? Ar<R>::neg(s.im) : s.im);
       });
@@ -339,12 +339,12 @@ __device__ __noinline__ void post_tile(const LineArgs& a, const cx<R>* buf, int 
     }
     case LK_C2C_F:
     case LK_C2C_I:
-      for_items<OY, MC>(a, nl, fk, [&](int L, int k) { stc(s_bout[L], k, buf[L * ldm + k]); });
+      for_items<OY, MC>(a, nl, fk, [&](int L, int k) { stc(s_bout[L], k, buf[L * ldm + pad(k)]); });
       break;
     case LK_C2R:
       for_items<OY, MC>(a, nl, fk, [&](int L, int k) {
         const long long b = s_bout[L];
-        cx<R> z = buf[L * ldm + k];
+        cx<R> z = buf[L * ldm + pad(k)];
         str(b, 2 * k, z.re);
         str(b, 2 * k + 1, z.im);
       });
@@ -355,7 +355,7 @@ __device__ __noinline__ void post_tile(const LineArgs& a, const cx<R>* buf, int 
       const bool dst = (kind == LK_DST3);
       for_items<OY, MC>(a, nl, fk, [&](int L, int k) {
         const long long b = s_bout[L];
-        cx<R> z = buf[L * ldm + k];
+        cx<R> z = buf[L * ldm + pad(k)];
         int j0 = 2 * k, j1 = 2 * k + 1;
         int s0 = j0 < M ? 2 * j0 : 2 * N - 1 - 2 * j0;
         int s1 = j1 < M ? 2 * j1 : 2 * N - 1 - 2 * j1;

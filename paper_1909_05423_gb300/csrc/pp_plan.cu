@@ -353,7 +353,7 @@ static void choose_shapes(pp_plan* p, const pp_plan_options* opt) {
     if (opt && opt->lines_x) lpc = std::min(lpc, opt->lines_x);
     lpc = std::min(lpc, kMaxLpc);
     lpc = std::min(lpc, nlines);
-    int ldm = M + 1;
+    int ldm = M + (M >> 5) + 1;  // one padding slot per 32 elements (see pad() in pp_fft.cuh)
     auto need = [&](int l) { return (size_t)l * ldm * cs + (size_t)M * cs; };
     while (lpc > 1 && need(lpc) > smem_cap) lpc--;
     p->threads_x = T;
@@ -381,7 +381,7 @@ static void choose_shapes(pp_plan* p, const pp_plan_options* opt) {
     if (opt && opt->cols_y) cols = std::min(cols, opt->cols_y);
     cols = std::min(cols, kMaxLpc / parts);
     cols = std::min(cols, ncols);
-    int ldm = M + 1;
+    int ldm = M + (M >> 5) + 1;
     auto need = [&](int c) { return (size_t)c * parts * ldm * cs + (size_t)M * cs; };
     while (cols > 1 && need(cols) > smem_cap) cols--;
     p->threads_y = T;
