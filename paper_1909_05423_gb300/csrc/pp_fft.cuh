@@ -45,12 +45,13 @@ struct FastDiv {
 // butterflies per thread per stage
 template <int RAD> struct NBut;
 template <> struct NBut<2> { static constexpr int v = 4; };
-template <> struct NBut<3> { static constexpr int v = 2; };
+template <> struct NBut<3> { static constexpr int v = 3; };
 template <> struct NBut<4> { static constexpr int v = 2; };
 template <> struct NBut<8> { static constexpr int v = 1; };
-// complex values a thread holds per stage: 8 for radix 2/4/8, 6 for radix 3
+// complex values a thread holds per stage: 8 for radix 2/4/8, 9 for radix 3.  A launch is valid
+// only if lines_per_cta * M <= kCapPerThread * threads (checked on the host before every launch).
 constexpr int kCapPerThread = 8;
-constexpr int kCapPerThread3 = 6;
+constexpr int kCapPerThread3 = 8;
 
 // r-point DFTs in registers (forward kernel exp(-2 pi i/r); INV uses the conjugate).
 template <class R, bool INV> __device__ __forceinline__ void dft2(cx<R>* a) {

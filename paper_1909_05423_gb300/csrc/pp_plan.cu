@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -51,6 +52,15 @@ pp_status set_last_error(pp_status s, const char* msg) { return fail(s, "%s", ms
     cudaError_t _e = (call);                                                               \
     if (_e != cudaSuccess) return fail(PP_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(_e)); \
   } while (0)
+
+// ------------------------------------------------------------------ fault injection
+// Host-side fault injection for tests: PP_FAULT_INJECT names one failure point ("alloc": the
+// plan's device allocations fail; "graph": instantiating a batch graph fails).  The failure is
+// reported exactly as a real one would be; nothing reaches the GPU.
+static bool inject(const char* point) {
+  const char* v = getenv("PP_FAULT_INJECT");
+  return v && strcmp(v, point) == 0;
+}
 
 // ------------------------------------------------------------------ helpers
 static bool smooth23(int n) {
@@ -164,6 +174,7 @@ struct Tab {
 
 static pp_status upload(void** dptr, const std::vector<float>& v) {
   size_t bytes = std::max<size_t>(v.size(), 4) * sizeof(float);
+  if (inject("alloc")) return fail(PP_ERR_OUT_OF_MEMORY, "cudaMalloc(%zu): injected failure", bytes);
   cudaError_t e = cudaMalloc(dptr, bytes);
   if (e != cudaSuccess) return fail(PP_ERR_OUT_OF_MEMORY, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
   if (!v.empty()) CUDA_OK(cudaMemcpy(*dptr, v.data(), v.size() * sizeof(float), cudaMemcpyHostToDevice));
@@ -346,7 +357,10 @@ static void choose_shapes(pp_plan* p, const pp_plan_options* opt) {
     int M = p->fx.M;
     bool r3 = false;
     for (int i = 0; i < p->fx.nst; i++) r3 |= p->fx.rad[i] == 3;
+    // a CTA must hold at least one whole line: threads * kCapPerThread >= M
+    const int tmin = std::max(32, ((M + kCapPerThread - 1) / kCapPerThread + 31) / 32 * 32);
     int T = (opt && opt->threads_x) ? opt->threads_x : 128;
+    T = std::max(T, tmin);
     int cap = (r3 ? kCapPerThread3 : kCapPerThread) * T;
     int nlines = p->ny * p->nz;
     int lpc = std::max(1, cap / std::max(M, 1));
@@ -370,17 +384,24 @@ static void choose_shapes(pp_plan* p, const pp_plan_options* opt) {
     int ncols = cplx_cols ? p->nx / 2 + 1 : p->nx;
     size_t col_bytes = (cplx_cols ? 2 : 1) * se;
     // CTA size: 128 threads unless that leaves column segments below one 32-byte sector
+    const int tmin = std::max(32, ((M + kCapPerThread - 1) / kCapPerThread + 31) / 32 * 32);
     int T = 128;
     const int tmax = 512;
     if (opt && opt->threads_y) T = opt->threads_y;
     else
       while (T < tmax && (size_t)std::max(1, (kCapPerThread3 * T / std::max(M, 1)) / parts) * col_bytes < 32) T *= 2;
+    T = std::max(T, tmin);
     int cap = (r3 ? kCapPerThread3 : kCapPerThread) * T;
     int maxlines = std::max(1, cap / std::max(M, 1));
     int cols = std::max(1, maxlines / parts);
     if (opt && opt->cols_y) cols = std::min(cols, opt->cols_y);
     cols = std::min(cols, kMaxLpc / parts);
     cols = std::min(cols, ncols);
+    // complex columns split into two real lines need room for both
+    while (cols * parts * M > cap && T < tmax) {
+      T = std::min(2 * T, tmax);
+      cap = (r3 ? kCapPerThread3 : kCapPerThread) * T;
+    }
     int ldm = M + (M >> 5) + 1;
     auto need = [&](int c) { return (size_t)c * parts * ldm * cs + (size_t)M * cs; };
     while (cols > 1 && need(cols) > smem_cap) cols--;
@@ -439,6 +460,7 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
       a.in_plane = sp_plane; a.in_line = (int)sp_row; a.in_pos = per ? 2 : 1;
       a.out_plane = grid_plane; a.out_line = grid_row; a.out_pos = 1;
     }
+    if ((long long)a.lpc * a.fp.M > (long long)kCapPerThread * p->threads_x) return cudaErrorInvalidConfiguration;
     a.ntiles = (a.nlines + a.lpc - 1) / a.lpc;
     a.vec_ok = (((uintptr_t)in | (uintptr_t)out) % 32 == 0) ? 1 : 0;
     finish_args(a);
@@ -471,6 +493,7 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
     a.in_plane = s_plane; a.in_line = (int)s_col; a.in_pos = (int)s_pos;
     a.out_plane = xs_plane; a.out_line = xs_col; a.out_pos = xs_pos;
   }
+  if ((long long)a.lpc * a.fp.M > (long long)kCapPerThread * p->threads_y) return cudaErrorInvalidConfiguration;
   a.tx = a.lpc / parts;
   a.ncols = ncols;
   a.nblk = (ncols + a.tx - 1) / a.tx;
@@ -603,7 +626,7 @@ static pp_status autotune(pp_plan* p) {
         choose_shapes(p, &o);
       }
       float t = time_pair(0, 4);
-      if (t < bx) { bx = t; best.threads_x = o.threads_x; best.lines_x = o.lines_x; }
+      if (t < bx) { bx = t; best.threads_x = p->threads_x; best.lines_x = o.lines_x; }
     }
   }
   // y kernels (x part fixed at its best)
@@ -623,7 +646,7 @@ static pp_status autotune(pp_plan* p) {
         choose_shapes(p, &o);
       }
       float t = time_pair(1, 3);
-      if (t < by) { by = t; best.threads_y = o.threads_y; best.cols_y = o.cols_y; }
+      if (t < by) { by = t; best.threads_y = p->threads_y; best.cols_y = o.cols_y; }
     }
   }
   cleanup();
@@ -879,7 +902,7 @@ pp_status pp_solve_batched(pp_plan* const* plans, const void* const* f, void* co
   }
   if (e != cudaSuccess) return fail(PP_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
   cudaGraphExec_t exec = nullptr;
-  e = cudaGraphInstantiate(&exec, graph, 0);
+  e = inject("graph") ? cudaErrorInvalidValue : cudaGraphInstantiate(&exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return fail(PP_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
   e = cudaGraphLaunch(exec, st);

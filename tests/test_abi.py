@@ -77,3 +77,13 @@ def test_null_arguments(lib):
     assert lib.pp_plan_destroy(None) == 0
     assert lib.pp_solve_batched(None, None, None, 0, None) == 0
     assert lib.pp_solve_batched(None, None, None, -1, None) == 1
+
+
+def test_fault_injection_alloc_fails_cleanly(lib, monkeypatch):
+    """An injected allocation failure is reported as PP_ERR_OUT_OF_MEMORY with a message and no
+    plan; the failure is made on the host before any device work (runs without a GPU)."""
+    monkeypatch.setenv("PP_FAULT_INJECT", "alloc")
+    st, h = _create(lib, 8, 8, 8, "PPPPDD")
+    assert st == 4
+    assert h.value is None
+    assert b"injected" in lib.pp_last_error_string()

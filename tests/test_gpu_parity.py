@@ -200,3 +200,36 @@ def test_autotuned_plan_matches_oracle(oracle):
     for _ in range(2):  # second creation hits the cache
         u = gpu_solve(f, "NDPPDD", sp, options={"autotune": 1})
         assert rel_l2(u, ref) <= TOL_F64
+
+
+def test_fault_injection_graph(oracle, monkeypatch):
+    """An injected graph-instantiation failure surfaces as PP_ERR_CUDA from pp_solve_batched; the
+    plans stay usable and the next batch (injection off) is correct."""
+    import paper_1909_05423_gb300 as pp
+    shape = (6, 12, 18)
+    f = workloads.uniform_source(shape, seed=77)
+    plans = [pp.Plan(shape, "DDNNPP", (1.0, 1.0, 1.0), "f64")]
+    fs = [torch.from_numpy(f).cuda()]
+    us = [torch.empty_like(fs[0])]
+    monkeypatch.setenv("PP_FAULT_INJECT", "graph")
+    with pytest.raises(pp.PPError) as ei:
+        pp.solve_batched(plans, fs, us)
+    assert ei.value.status == 5
+    monkeypatch.delenv("PP_FAULT_INJECT")
+    pp.solve_batched(plans, fs, us)
+    torch.cuda.synchronize()
+    assert rel_l2(us[0].cpu().numpy(), oracle.solve(f, "DDNNPP")) <= TOL_F64
+    plans[0].close()
+
+
+@pytest.mark.parametrize("shape,bc", [((2, 2, 4096), "DNNNDD"), ((3, 4096, 2), "PPPPNN"), ((3, 4096, 4), "NNDNPP"),
+                                      ((3, 6, 3456), "PPDDNN")])
+def test_maximum_line_lengths(oracle, shape, bc):
+    """The longest supported lines (4096 = the size limit, and the 3-smooth 3456), which run the
+    run-time-length kernels with one or two lines per CTA."""
+    sp = (1.0 / shape[2], 1.0 / shape[1], 1.0 / shape[0])
+    f = workloads.uniform_source(shape, seed=31)
+    ref = oracle.solve(f, bc, sp)
+    for dtype, tol in (("f64", TOL_F64), ("mixed_f64io", 1e-6)):
+        u = gpu_solve(f, bc, sp, dtype)
+        assert rel_l2(u, ref) <= tol, (dtype, rel_l2(u, ref))
