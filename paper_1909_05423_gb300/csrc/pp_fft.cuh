@@ -149,10 +149,16 @@ __device__ __forceinline__ void fft_stage(cx<R>* buf, int nlines, int ldm, int s
       const int o = q + s * RAD * p;
       y[pad(o)] = a[i][0];
       const int ps = p * s;
+      if (s == nbl) {
+        // last stage: p = 0, every twiddle is 1
 #pragma unroll
-      for (int t = 1; t < RAD; t++) {
-        cx<R> w = tw[ps * t];
-        y[pad(o + s * t)] = INV ? cmulc(a[i][t], w) : cmul(a[i][t], w);
+        for (int t = 1; t < RAD; t++) y[pad(o + s * t)] = a[i][t];
+      } else {
+#pragma unroll
+        for (int t = 1; t < RAD; t++) {
+          cx<R> w = tw[ps * t];
+          y[pad(o + s * t)] = INV ? cmulc(a[i][t], w) : cmul(a[i][t], w);
+        }
       }
     }
   }
@@ -212,11 +218,17 @@ __device__ __forceinline__ void fft_stage_ct(cx<R>* buf, int nlines, int ldm, co
       cx<R>* y = buf + line * ldm;
       const int o = q + S * RAD * p;
       y[pad(o)] = a[i][0];
-      const int ps = p * S;
+      if constexpr (S * RAD == MC) {
+        // last stage: p = 0, every twiddle is 1
 #pragma unroll
-      for (int t = 1; t < RAD; t++) {
-        cx<R> w = tw[ps * t];
-        y[pad(o + S * t)] = INV ? cmulc(a[i][t], w) : cmul(a[i][t], w);
+        for (int t = 1; t < RAD; t++) y[pad(o + S * t)] = a[i][t];
+      } else {
+        const int ps = p * S;
+#pragma unroll
+        for (int t = 1; t < RAD; t++) {
+          cx<R> w = tw[ps * t];
+          y[pad(o + S * t)] = INV ? cmulc(a[i][t], w) : cmul(a[i][t], w);
+        }
       }
     }
   }

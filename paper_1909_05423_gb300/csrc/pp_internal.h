@@ -44,16 +44,18 @@ struct LineArgs {
   long long out_line, out_pos;  // output: stride between consecutive lines / positions (reals)
   int ntiles;         // tiles of the launch (x: lpc rows; y: one plane x tx columns)
   int vec_ok;         // x lines: both arrays 32-byte aligned (vectorised pre/post allowed)
+  int vec_y;          // y tiles: rows contiguous and 16-byte aligned, lpc a multiple of the vector width
   int tx, ncols, nblk;  // y: columns per tile, columns per plane, column blocks per plane
   const void* tw;     // stage twiddles w_M^j, j < M (complex, arithmetic type)
   const void* aux;    // pre/post twiddles (complex, arithmetic type), layout per kind
   FftPlan fp;
-  FastDiv fd_kpre;    // number of pre-processing items per line (M)
+  FastDiv fd_kpre;    // number of pre-processing items per line (M; M/2 + 1 for Hermitian pairs)
   FastDiv fd_kpost;   // number of post-processing items per line
   FastDiv fd_lpc;     // lines per CTA
   FastDiv fd_lpp;     // lines per plane
   FastDiv fd_parts;   // 1 or 2
   FastDiv fd_nblk;    // column blocks per plane
+  FastDiv fd_gpc;     // y: groups of vector-width adjacent lines per CTA
 };
 constexpr int kMaxLpc = 512;  // lines per CTA (bounded so the per-line bases fit in shared memory)
 

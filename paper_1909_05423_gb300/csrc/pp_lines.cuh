@@ -108,11 +108,65 @@ template <> struct Vec<float, float> {
   }
 };
 
+// 16-byte access to V adjacent reals of a y-tile row (4 FP32 or 2 double-float spill reals).
+template <class R, class S> struct VecN;
+template <> struct VecN<float, float> {
+  static constexpr int V = 4;
+  __device__ static __forceinline__ void ld(const float* p, long long o, float* v) {
+    float4 a = __ldg(reinterpret_cast<const float4*>(p + o));
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  }
+  __device__ static __forceinline__ void st(float* p, long long o, const float* v) {
+    *reinterpret_cast<float4*>(p + o) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <> struct VecN<df, float2> {
+  static constexpr int V = 2;
+  __device__ static __forceinline__ void ld(const float2* p, long long o, df* v) {
+    float4 a = __ldg(reinterpret_cast<const float4*>(p + o));
+    v[0] = df{a.x, a.y}; v[1] = df{a.z, a.w};
+  }
+  __device__ static __forceinline__ void st(float2* p, long long o, const df* v) {
+    *reinterpret_cast<float4*>(p + o) = make_float4(v[0].hi, v[0].lo, v[1].hi, v[1].lo);
+  }
+};
+// nv (<= V) adjacent reals: one vector access for a full group, scalar accesses for a partial one
+template <class R, class S> __device__ __forceinline__ void ldn(const S* p, long long o, int nv, R* v) {
+  constexpr int V = VecN<R, S>::V;
+  if (nv == V) { VecN<R, S>::ld(p, o, v); return; }
+#pragma unroll
+  for (int i = 0; i < V; i++) v[i] = (i < nv) ? Io<R, S>::ld(p, o + i) : Ar<R>::zero();
+}
+template <class R, class S> __device__ __forceinline__ void stn(S* p, long long o, int nv, const R* v) {
+  constexpr int V = VecN<R, S>::V;
+  if (nv == V) { VecN<R, S>::st(p, o, v); return; }
+#pragma unroll
+  for (int i = 0; i < V; i++)
+    if (i < nv) Io<R, S>::st(p, o + i, v[i]);
+}
+
+// y tiles with contiguous rows: visit (group of V adjacent lines starting at L0, item k); consecutive
+// threads take consecutive groups, so a warp's accesses are runs of 16-byte vectors.  nv = lines of
+// the group (V, or fewer for the last group of a partial tile).  KC: compile-time item count (0: fdk).
+template <int V, int KC, class F>
+__device__ __forceinline__ void for_groups(const LineArgs& a, int nl, const FastDiv& fdk, F&& fn) {
+  const int K = KC ? KC : (int)fdk.d;
+  const int G = (int)a.fd_gpc.d;
+  const int tot = G * K;
+#pragma unroll 2
+  for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+    const unsigned q = a.fd_gpc.div((unsigned)t);
+    const int L0 = (t - (int)q * G) * V;
+    if (L0 >= nl) continue;
+    fn(L0, (int)q, min(V, nl - L0));
+  }
+}
+
 template <class R, class SI> struct SrcGlobal {
   using elem_t = SI;
   const SI* in;
   const long long* bases;  // per-line bases (shared memory)
-  long long pos;
+  long long pos;           // stride between positions of a line
   __device__ __forceinline__ long long base(int L) const { return bases[L]; }
   __device__ __forceinline__ R ld(long long b, int j) const { return Io<R, SI>::ld(in, b + (long long)j * pos); }
 };
@@ -169,6 +223,88 @@ __device__ __noinline__ void pre_tile(const LineArgs& a, const Src src, int nl, 
       }
     }
   }
+  if constexpr (OY) {
+    if (a.vec_y) {
+      // real y lines of a contiguous tile row: V adjacent lines per item, 16-byte loads
+      using SI = typename Src::elem_t;
+      constexpr int V = VecN<R, SI>::V;
+      const long long pos = src.pos;
+      if (kind == LK_DCT2 || kind == LK_DST2) {
+        const bool dst = (kind == LK_DST2);
+        for_groups<V, MC>(a, nl, fk, [&](int L0, int k, int nv) {
+          const long long b = src.base(L0);
+          const int j0 = 2 * k, j1 = 2 * k + 1;
+          const int s0 = j0 < M ? 2 * j0 : 2 * N - 1 - 2 * j0;
+          const int s1 = j1 < M ? 2 * j1 : 2 * N - 1 - 2 * j1;
+          R v0[V], v1[V];
+          ldn<R>(src.in, b + s0 * pos, nv, v0);
+          ldn<R>(src.in, b + s1 * pos, nv, v1);
+#pragma unroll
+          for (int v = 0; v < V; v++) {
+            if (v < nv) {
+              R x0 = v0[v], x1 = v1[v];
+              if (dst) {
+                if (j0 >= M) x0 = Ar<R>::neg(x0);
+                if (j1 >= M) x1 = Ar<R>::neg(x1);
+              }
+              buf[(L0 + v) * ldm + pad(k)] = cx<R>{x0, x1};
+            }
+          }
+        });
+        return;
+      }
+      if (kind == LK_DCT4 || kind == LK_DST4) {
+        const bool c4 = (kind == LK_DCT4);
+        for_groups<V, MC>(a, nl, fk, [&](int L0, int k, int nv) {
+          const long long b = src.base(L0);
+          R e[V], o[V];
+          ldn<R>(src.in, b + (long long)(2 * k) * pos, nv, e);
+          ldn<R>(src.in, b + (long long)(N - 1 - 2 * k) * pos, nv, o);
+          const cx<R> w = aux[k];  // exp(-i pi (4k+1) / 4N)
+#pragma unroll
+          for (int v = 0; v < V; v++)
+            if (v < nv) buf[(L0 + v) * ldm + pad(k)] = cmul(c4 ? cx<R>{e[v], o[v]} : cx<R>{o[v], e[v]}, w);
+        });
+        return;
+      }
+      if (kind == LK_DCT3 || kind == LK_DST3) {
+        // as the scalar Hermitian-pair path below, V lines per item
+        const cx<R>* w4 = aux + (M + 1);
+        const bool c3 = (kind == LK_DCT3);
+        for_groups<V, (MC ? MC / 2 + 1 : 0)>(a, nl, fk, [&](int L0, int k, int nv) {
+          const long long b = src.base(L0);
+          auto row = [&](int j) -> long long { return (long long)(c3 ? j : N - 1 - j) * pos; };
+          R y0[V], y1[V], y2[V], y3[V];  // Y_k, Y_{N-k} (Y_N = 0), Y_{M-k}, Y_{M+k}
+          ldn<R>(src.in, b + row(k), nv, y0);
+          if (k > 0) {
+            ldn<R>(src.in, b + row(N - k), nv, y1);
+          } else {
+#pragma unroll
+            for (int v = 0; v < V; v++) y1[v] = Ar<R>::zero();
+          }
+          ldn<R>(src.in, b + row(M - k), nv, y2);
+          ldn<R>(src.in, b + row(M + k), nv, y3);
+          const cx<R> wk = w4[k], wm = w4[M - k], ak = aux[k];
+          const int km = M - k;
+#pragma unroll
+          for (int v = 0; v < V; v++) {
+            if (v < nv) {
+              cx<R> Xk = cmulc(cx<R>{y0[v], Ar<R>::neg(y1[v])}, wk);
+              cx<R> Xm = cmulc(cx<R>{y2[v], Ar<R>::neg(y3[v])}, wm);
+              if (k == 0) { Xk.im = Ar<R>::zero(); Xm.im = Ar<R>::zero(); }
+              cx<R> Xc = cconj(Xm);
+              cx<R> E = cadd(Xk, Xc);
+              cx<R> O = cmulc(csub(Xk, Xc), ak);
+              cx<R>* zl = buf + (L0 + v) * ldm;
+              zl[pad(k)] = cx<R>{Ar<R>::sub(E.re, O.im), Ar<R>::add(E.im, O.re)};
+              if (k > 0 && km != k) zl[pad(km)] = cx<R>{Ar<R>::add(E.re, O.im), Ar<R>::sub(O.re, E.im)};
+            }
+          }
+        });
+        return;
+      }
+    }
+  }
   switch (kind) {
     case LK_R2C:
       for_items<OY, MC>(a, nl, fk, [&](int L, int k) {
@@ -214,10 +350,12 @@ __device__ __noinline__ void pre_tile(const LineArgs& a, const Src src, int nl, 
     case LK_DST3: {
       // Hermitian pair (X_k, X_{M-k}) -> Z_k = E + i O, E = X_k + conj X_{M-k},
       // O = (X_k - conj X_{M-k}) exp(+2 pi i k / N); imaginary parts of X_0, X_M dropped.
+      // The partner comes from the same two inputs: E_{M-k} = conj E and O_{M-k} = conj O, so
+      // Z_{M-k} = (E.re + O.im) + i (O.re - E.im); item k <= M/2 writes Z_k and Z_{M-k}.
       // DCT-III/DST-III first form V_j = exp(+i pi j / 2N) (Y_j - i Y_{N-j}), Y_N = 0
       // (DST-III reads Y reversed).
       const cx<R>* w4 = aux + (M + 1);
-      for_items<OY, MC>(a, nl, fk, [&](int L, int k) {
+      for_items<OY, (MC ? MC / 2 + 1 : 0)>(a, nl, fk, [&](int L, int k) {
         auto b = src.base(L);
         cx<R> Xk, Xm;
         if (kind == LK_C2R) {
@@ -238,6 +376,8 @@ __device__ __noinline__ void pre_tile(const LineArgs& a, const Src src, int nl, 
         cx<R> E = cadd(Xk, Xc);
         cx<R> O = cmulc(csub(Xk, Xc), aux[k]);  // * conj(w_N^k)
         buf[L * ldm + pad(k)] = cx<R>{Ar<R>::sub(E.re, O.im), Ar<R>::add(E.im, O.re)};
+        const int km = M - k;
+        if (k > 0 && km != k) buf[L * ldm + pad(km)] = cx<R>{Ar<R>::add(E.re, O.im), Ar<R>::sub(O.re, E.im)};
       });
       break;
     }
@@ -301,28 +441,114 @@ __device__ __noinline__ void post_tile(const LineArgs& a, const cx<R>* buf, int 
       }
     }
   }
+  if constexpr (OY) {
+    if (a.vec_y) {
+      // real y lines of a contiguous tile row: V adjacent lines per item, 16-byte stores
+      constexpr int V = VecN<R, SO>::V;
+      if (kind == LK_DCT2 || kind == LK_DST2) {
+        // as the scalar Hermitian-pair path below, V lines per item
+        const bool dst = (kind == LK_DST2);
+        for_groups<V, (MC ? MC / 2 + 1 : 0)>(a, nl, fk, [&](int L0, int k, int nv) {
+          const long long b = s_bout[L0];
+          const int km = M - k;
+          const cx<R> ak = aux[k], wk = aux[M + 1 + k], wm = aux[M + 1 + km];
+          R r0[V], r1[V], r2[V], r3[V];
+#pragma unroll
+          for (int v = 0; v < V; v++) {
+            if (v < nv) {
+              const cx<R>* zl = buf + (L0 + v) * ldm;
+              cx<R> Zk = zl[pad(k)];
+              cx<R> Zc = cconj(zl[pad(k == 0 ? 0 : km)]);
+              cx<R> E = chalf(cadd(Zk, Zc));
+              cx<R> dd = csub(Zk, Zc);
+              cx<R> P = cmul(chalf(cx<R>{dd.im, Ar<R>::neg(dd.re)}), ak);
+              cx<R> W0 = cmul(cadd(E, P), wk);
+              cx<R> W1 = cmul(cconj(csub(E, P)), wm);
+              r0[v] = W0.re; r1[v] = Ar<R>::neg(W0.im);
+              r2[v] = W1.re; r3[v] = Ar<R>::neg(W1.im);
+            } else {
+              r0[v] = r1[v] = r2[v] = r3[v] = Ar<R>::zero();
+            }
+          }
+          auto i0 = [&](int kk) -> long long { return (long long)(dst ? N - 1 - kk : kk) * op; };
+          auto i1 = [&](int kk) -> long long { return (long long)(dst ? kk - 1 : N - kk) * op; };
+          stn<R>(out, b + i0(k), nv, r0);
+          if (k >= 1 && k < M) stn<R>(out, b + i1(k), nv, r1);
+          if (km != k) {
+            stn<R>(out, b + i0(km), nv, r2);
+            if (km >= 1 && km < M) stn<R>(out, b + i1(km), nv, r3);
+          }
+        });
+        return;
+      }
+      if (kind == LK_DCT3 || kind == LK_DST3) {
+        const bool dst = (kind == LK_DST3);
+        for_groups<V, MC>(a, nl, fk, [&](int L0, int k, int nv) {
+          const long long b = s_bout[L0];
+          const int j0 = 2 * k, j1 = 2 * k + 1;
+          const int s0 = j0 < M ? 2 * j0 : 2 * N - 1 - 2 * j0;
+          const int s1 = j1 < M ? 2 * j1 : 2 * N - 1 - 2 * j1;
+          R r0[V], r1[V];
+#pragma unroll
+          for (int v = 0; v < V; v++) {
+            cx<R> z = (v < nv) ? buf[(L0 + v) * ldm + pad(k)] : cx<R>{Ar<R>::zero(), Ar<R>::zero()};
+            r0[v] = (dst && j0 >= M) ? Ar<R>::neg(z.re) : z.re;
+            r1[v] = (dst && j1 >= M) ? Ar<R>::neg(z.im) : z.im;
+          }
+          stn<R>(out, b + (long long)s0 * op, nv, r0);
+          stn<R>(out, b + (long long)s1 * op, nv, r1);
+        });
+        return;
+      }
+      if (kind == LK_DCT4 || kind == LK_DST4) {
+        const bool c4 = (kind == LK_DCT4);
+        for_groups<V, MC>(a, nl, fk, [&](int L0, int k, int nv) {
+          const long long b = s_bout[L0];
+          const cx<R> w = aux[M + k];  // exp(-i pi k / N)
+          R r0[V], r1[V];
+#pragma unroll
+          for (int v = 0; v < V; v++) {
+            cx<R> sv = (v < nv) ? cmul(buf[(L0 + v) * ldm + pad(k)], w) : cx<R>{Ar<R>::zero(), Ar<R>::zero()};
+            r0[v] = sv.re;
+            r1[v] = c4 ? Ar<R>::neg(sv.im) : sv.im;
+          }
+          stn<R>(out, b + (long long)(2 * k) * op, nv, r0);
+          stn<R>(out, b + (long long)(N - 1 - 2 * k) * op, nv, r1);
+        });
+        return;
+      }
+    }
+  }
   switch (kind) {
     case LK_R2C:
     case LK_DCT2:
     case LK_DST2: {
-      // X_k = E_k + w_N^k O_k from the Hermitian pair (Z_k, Z_{M-k}); DCT-II: W = exp(-i pi k/2N) X_k,
+      // X_k = E_k + w_N^k O_k from the Hermitian pair (Z_k, Z_{M-k}), E_k = (Z_k + conj Z_{M-k})/2,
+      // O_k = (Z_k - conj Z_{M-k})/2i.  The partner needs no second pass: E_{M-k} = conj E_k,
+      // O_{M-k} = conj O_k and w_N^{M-k} = -conj w_N^k give X_{M-k} = conj(E_k - w_N^k O_k); item
+      // k <= M/2 emits X_k and X_{M-k} (k = 0: X_0 and X_M).  DCT-II: W = exp(-i pi k/2N) X_k,
       // Y_k = Re W, Y_{N-k} = -Im W; DST-II writes the DCT-II of the sign-alternated line reversed.
-      for_items<OY, 0>(a, nl, fk, [&](int L, int k) {
+      for_items<OY, (MC ? MC / 2 + 1 : 0)>(a, nl, fk, [&](int L, int k) {
         const long long b = s_bout[L];
         const cx<R>* zl = buf + L * ldm;
-        cx<R> Zk = zl[pad(k == M ? 0 : k)];
-        cx<R> Zm = zl[pad(k == 0 ? 0 : M - k)];
+        const int km = M - k;
+        cx<R> Zk = zl[pad(k)];
+        cx<R> Zm = zl[pad(k == 0 ? 0 : km)];
         cx<R> Zc = cconj(Zm);
         cx<R> E = chalf(cadd(Zk, Zc));
         cx<R> dd = csub(Zk, Zc);
         cx<R> O = chalf(cx<R>{dd.im, Ar<R>::neg(dd.re)});  // (Zk - conj Zm) / (2i)
-        cx<R> X = cadd(E, cmul(O, aux[k]));               // + w_N^k O
-        if (kind == LK_R2C) { stc(b, k, X); return; }
-        cx<R> W = cmul(X, aux[M + 1 + k]);                 // exp(-i pi k / 2N)
-        int i0 = k, i1 = N - k;
-        if (kind == LK_DST2) { i0 = N - 1 - k; i1 = k - 1; }
-        str(b, i0, W.re);
-        if (k >= 1 && k < M) str(b, i1, Ar<R>::neg(W.im));
+        cx<R> P = cmul(O, aux[k]);                         // w_N^k O
+        auto emit = [&](int kk, cx<R> X) {
+          if (kind == LK_R2C) { stc(b, kk, X); return; }
+          cx<R> W = cmul(X, aux[M + 1 + kk]);              // exp(-i pi kk / 2N)
+          int i0 = kk, i1 = N - kk;
+          if (kind == LK_DST2) { i0 = N - 1 - kk; i1 = kk - 1; }
+          str(b, i0, W.re);
+          if (kk >= 1 && kk < M) str(b, i1, Ar<R>::neg(W.im));
+        };
+        emit(k, cadd(E, P));
+        if (km != k) emit(km, cconj(csub(E, P)));
       });
       break;
     }

@@ -417,12 +417,14 @@ enum { ST_F64 = 0, ST_F32 = 1, ST_SPILL = 2 };
 // division helpers of one launch
 static void finish_args(LineArgs& a) {
   int M = a.fp.M, N = a.N, K;
+  // Hermitian-pair kinds handle k and M-k in one item, k <= M/2
   switch (a.kind) {
-    case LK_R2C: case LK_DCT2: case LK_DST2: K = M + 1; break;
+    case LK_R2C: case LK_DCT2: case LK_DST2: K = M / 2 + 1; break;
     case LK_C2C_F: case LK_C2C_I: K = N; break;
     default: K = M;
   }
-  a.fd_kpre = FastDiv::make((unsigned)M);
+  const bool herm_in = (a.kind == LK_C2R || a.kind == LK_DCT3 || a.kind == LK_DST3);
+  a.fd_kpre = FastDiv::make((unsigned)(herm_in ? M / 2 + 1 : M));
   a.fd_kpost = FastDiv::make((unsigned)K);
   a.fd_lpc = FastDiv::make((unsigned)a.lpc);
   a.fd_lpp = FastDiv::make((unsigned)a.lines_per_plane);
@@ -463,6 +465,7 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
     if ((long long)a.lpc * a.fp.M > (long long)kCapPerThread * p->threads_x) return cudaErrorInvalidConfiguration;
     a.ntiles = (a.nlines + a.lpc - 1) / a.lpc;
     a.vec_ok = (((uintptr_t)in | (uintptr_t)out) % 32 == 0) ? 1 : 0;
+    a.fd_gpc = FastDiv::make(1u);
     finish_args(a);
     return launch_lines_impl(a, dfm, 0, io_in, io_out, p->threads_x, 0, 0, st);
   }
@@ -498,6 +501,17 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
   a.ncols = ncols;
   a.nblk = (ncols + a.tx - 1) / a.tx;
   a.ntiles = a.nblk * p->nz;
+  {
+    // 16-byte vectors of V adjacent real lines: the tile row must be contiguous (line L at real
+    // offset L) and every vector start aligned (checked through all strides and both pointers)
+    const int V = dfm ? 2 : 4;
+    const bool real_lines = (a.kind == LK_DCT2 || a.kind == LK_DST2 || a.kind == LK_DCT3 || a.kind == LK_DST3 ||
+                             a.kind == LK_DCT4 || a.kind == LK_DST4);
+    a.vec_y = (real_lines && a.in_line == parts && a.out_line == parts && a.lpc % V == 0 && a.in_plane % V == 0 &&
+               a.out_plane % V == 0 && a.in_pos % V == 0 && a.out_pos % V == 0 &&
+               ((uintptr_t)in | (uintptr_t)out) % 16 == 0) ? 1 : 0;
+    a.fd_gpc = FastDiv::make((unsigned)std::max(1, a.lpc / V));
+  }
   finish_args(a);
   a.fd_nblk = FastDiv::make((unsigned)a.nblk);
   return launch_lines_impl(a, dfm, 1, io_in, io_out, p->threads_y, 0, 0, st);
