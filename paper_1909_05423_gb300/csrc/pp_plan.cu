@@ -26,7 +26,7 @@
 namespace pp {
 cudaError_t launch_lines_impl(const LineArgs& a, bool df_arith, int oy, int sin, int sout, int threads, size_t smem,
                               int grid, cudaStream_t st);
-cudaError_t launch_zsolve_impl(const ZArgs& a, bool df_spill, cudaStream_t st);
+cudaError_t launch_zsolve_impl(const ZArgs& a, bool df_spill, bool zper, cudaStream_t st);
 }  // namespace pp
 
 using namespace pp;
@@ -535,7 +535,7 @@ cudaError_t launch_zsolve(const pp_plan* p, void* data, int transpose, cudaStrea
   a.qtab = p->d_qtab;
   split2(p->zscale, a.scale);
   a.transpose = transpose;
-  return launch_zsolve_impl(a, p->dtype == PP_F64, st);
+  return launch_zsolve_impl(a, p->dtype == PP_F64, p->bc[4] == PP_BC_PERIODIC, st);
 }
 }  // namespace pp
 

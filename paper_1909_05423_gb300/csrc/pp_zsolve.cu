@@ -30,22 +30,57 @@
 
 namespace pp {
 
-template <class S> struct ZIo;
-template <> struct ZIo<float2> {
-  __device__ static __forceinline__ df ld(const float2* p) { float2 v = *p; return df{v.x, v.y}; }
-  __device__ static __forceinline__ void st(float2* p, df v) { *p = make_float2(v.hi, v.lo); }
-};
-template <> struct ZIo<float> {
-  __device__ static __forceinline__ df ld(const float* p) { return df{*p, 0.0f}; }
-  __device__ static __forceinline__ void st(float* p, df v) { *p = df_to_f32(v); }
-};
+// raw spill value -> double-float, and back
+__device__ __forceinline__ df zcvt(float2 v) { return df{v.x, v.y}; }
+__device__ __forceinline__ df zcvt(float v) { return df{v, 0.0f}; }
+__device__ __forceinline__ void zput(float2* p, df v) { *p = make_float2(v.hi, v.lo); }
+__device__ __forceinline__ void zput(float* p, df v) { *p = df_to_f32(v); }
 
 __device__ __forceinline__ df f2df(const float* v) { return df{v[0], v[1]}; }
 __device__ __forceinline__ df f2df(float2 v) { return df{v.x, v.y}; }
 
-constexpr int ZU = 8;  // loads issued ahead in each sweep
+// Planes per batch.  Each sweep loads the next batch before it computes the current one, so a
+// thread always has one batch of loads in flight (the sweeps are bound by loads in flight).
+constexpr int ZU = 8;
 
+// raw values of planes k0 + step*u, u < ZU, that lie in [0, n)
 template <class S>
+__device__ __forceinline__ void zload(S* v, const S* base, long long P, int k0, int step, int n) {
+#pragma unroll
+  for (int u = 0; u < ZU; u++) {
+    const int k = k0 + step * u;
+    if (k >= 0 && k < n) v[u] = base[(long long)k * P];
+  }
+}
+
+// The singular mode: remove the source mean, pin u_0 = 0, solve rows 1..n-1, shift to zero mean.
+template <class S>
+__device__ __noinline__ void z_singular(S* base, long long P, int n, df scale, const float2* wt) {
+  df sum = df{0.f, 0.f};
+  for (int k = 0; k < n; k++) sum = sum + zcvt(base[k * P]);
+  df mean = sum * df_rcp(df{(float)n, 0.f});
+  // rows 1..n-1 of the pinned system; multipliers of the sub-system in the table
+  df g = df{0.f, 0.f};
+  for (int k = 1; k < n; k++) {
+    df d = (zcvt(base[k * P]) - mean) * scale;
+    g = (d - g) * f2df(__ldg(wt + (k - 1)));
+    zput(base + k * P, g);
+  }
+  df u = df{0.f, 0.f};
+  df usum = df{0.f, 0.f};
+  for (int k = n - 1; k >= 1; k--) {
+    df gk = zcvt(base[k * P]);
+    u = (k == n - 1) ? gk : gk - f2df(__ldg(wt + (k - 1))) * u;
+    usum = usum + u;
+    zput(base + k * P, u);
+  }
+  df umean = usum * df_rcp(df{(float)n, 0.f});
+  zput(base, -umean);
+  for (int k = 1; k < n; k++) zput(base + k * P, zcvt(base[k * P]) - umean);
+}
+
+// MODE 0: Thomas; 1: periodic z (Sherman-Morrison); 2: transposed factorisation (adjoint).
+template <class S, int MODE>
 __global__ void __launch_bounds__(256) k_zsolve(const ZArgs a) {
   long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= a.nreal) return;
@@ -54,70 +89,48 @@ __global__ void __launch_bounds__(256) k_zsolve(const ZArgs a) {
   const int col = (int)(s - (long long)row * a.row_reals);
   if (col >= a.row_valid) return;
   const long long mi = (long long)row * a.row_modes + (a.cplx ? (col >> 1) : col);
-  const ZMode m = a.modes[mi];
+  const ZMode& m = a.modes[mi];
   S* base = reinterpret_cast<S*>(a.data) + s;
   const long long P = a.plane;
   const int n = a.nz;
   const df scale = df{a.scale[0], a.scale[1]};
-  const df winf = f2df(m.winf), wlast = f2df(m.wlast);
   const float2* wt = a.wtab + m.woff;
-  auto W = [&](int k) -> df {
-    if (k == n - 1) return wlast;
-    if (k < m.wlen) return f2df(__ldg(wt + k));
-    return winf;
-  };
-
-  if (m.flags & ZF_SINGULAR) {
-    // mean of the source
-    df sum = df{0.f, 0.f};
-    for (int k = 0; k < n; k++) sum = sum + ZIo<S>::ld(base + k * P);
-    df mean = sum * df_rcp(df{(float)n, 0.f});
-    // rows 1..n-1 of the pinned system (u_0 = 0); multipliers of the sub-system in the table
-    df g = df{0.f, 0.f};
-    for (int k = 1; k < n; k++) {
-      df d = (ZIo<S>::ld(base + k * P) - mean) * scale;
-      df w = f2df(__ldg(wt + (k - 1)));
-      g = (d - g) * w;
-      ZIo<S>::st(base + k * P, g);
-    }
-    df u = df{0.f, 0.f};
-    df usum = df{0.f, 0.f};
-    for (int k = n - 1; k >= 1; k--) {
-      df gk = ZIo<S>::ld(base + k * P);
-      df w = f2df(__ldg(wt + (k - 1)));
-      u = (k == n - 1) ? gk : gk - w * u;
-      usum = usum + u;
-      ZIo<S>::st(base + k * P, u);
-    }
-    df umean = usum * df_rcp(df{(float)n, 0.f});
-    ZIo<S>::st(base, -umean);
-    for (int k = 1; k < n; k++) ZIo<S>::st(base + k * P, ZIo<S>::ld(base + k * P) - umean);
+  const int flags = m.flags;
+  if (flags & ZF_SINGULAR) {
+    z_singular<S>(base, P, n, scale, wt);
     return;
   }
+  const df winf = f2df(m.winf), wlast = f2df(m.wlast);
+  const int wlen = m.wlen;
+  auto W = [&](int k) -> df {
+    if (k == n - 1) return wlast;
+    if (k < wlen) return f2df(__ldg(wt + k));
+    return winf;
+  };
+  S cur[ZU], nxt[ZU];
 
-  const bool periodic = (m.flags & ZF_PERIODIC) != 0;
-  const float2* qt = a.qtab + m.qoff;
-  const int qlen = m.qlen;
-
-  if (!a.transpose || periodic) {
+  if constexpr (MODE != 2) {
+    constexpr bool periodic = (MODE == 1);
+    const float2* qt = a.qtab + m.qoff;
+    const int qlen = periodic ? m.qlen : 0;
     // forward elimination g_k = (s d_k - g_{k-1}) w_k; periodic: y0 = sum q_k s d_k
     df g = df{0.f, 0.f};
     df y0 = df{0.f, 0.f};
+    zload(cur, base, P, 0, 1, n);
     for (int k0 = 0; k0 < n; k0 += ZU) {
-      df dv[ZU];
-#pragma unroll
-      for (int u = 0; u < ZU; u++)
-        if (k0 + u < n) dv[u] = ZIo<S>::ld(base + (k0 + u) * P);
+      if (k0 + ZU < n) zload(nxt, base, P, k0 + ZU, 1, n);
 #pragma unroll
       for (int u = 0; u < ZU; u++) {
-        int k = k0 + u;
+        const int k = k0 + u;
         if (k < n) {
-          df d = dv[u] * scale;
+          df d = zcvt(cur[u]) * scale;
           g = (d - g) * W(k);
           if (periodic && k < qlen) y0 = y0 + f2df(__ldg(qt + k)) * d;
-          ZIo<S>::st(base + k * P, g);
+          zput(base + k * P, g);
         }
       }
+#pragma unroll
+      for (int u = 0; u < ZU; u++) cur[u] = nxt[u];
     }
     // back substitution u_k = g_k - w_k u_{k+1}
     df c = df{0.f, 0.f}, gam = df{0.f, 0.f};
@@ -127,17 +140,16 @@ __global__ void __launch_bounds__(256) k_zsolve(const ZArgs a) {
     }
     df u = df{0.f, 0.f};
     df p = wlast;
+    zload(cur, base, P, n - 1, -1, n);
     for (int k0 = n - 1; k0 >= 0; k0 -= ZU) {
-      df gv[ZU];
-#pragma unroll
-      for (int t = 0; t < ZU; t++)
-        if (k0 - t >= 0) gv[t] = ZIo<S>::ld(base + (k0 - t) * P);
+      if (k0 - ZU >= 0) zload(nxt, base, P, k0 - ZU, -1, n);
 #pragma unroll
       for (int t = 0; t < ZU; t++) {
-        int k = k0 - t;
+        const int k = k0 - t;
         if (k >= 0) {
-          df wk = W(k);
-          u = (k == n - 1) ? gv[t] : gv[t] - wk * u;
+          const df wk = W(k);
+          const df gk = zcvt(cur[t]);
+          u = (k == n - 1) ? gk : gk - wk * u;
           df outv = u;
           if (periodic) {
             if (k < n - 1) p = -(wk * p);
@@ -145,54 +157,66 @@ __global__ void __launch_bounds__(256) k_zsolve(const ZArgs a) {
             if (k < qlen) zk = zk + gam * f2df(__ldg(qt + k));
             outv = u - c * zk;
           }
-          ZIo<S>::st(base + k * P, outv);
+          zput(base + k * P, outv);
         }
       }
+#pragma unroll
+      for (int t = 0; t < ZU; t++) cur[t] = nxt[t];
     }
   } else {
     // transposed factorisation T^T = U^T L^T:  h_k = s d_k - w_{k-1} h_{k-1},  x_k = (h_k - x_{k+1}) w_k
     df h = df{0.f, 0.f};
     df wprev = df{0.f, 0.f};
+    zload(cur, base, P, 0, 1, n);
     for (int k0 = 0; k0 < n; k0 += ZU) {
-      df dv[ZU];
-#pragma unroll
-      for (int u = 0; u < ZU; u++)
-        if (k0 + u < n) dv[u] = ZIo<S>::ld(base + (k0 + u) * P);
+      if (k0 + ZU < n) zload(nxt, base, P, k0 + ZU, 1, n);
 #pragma unroll
       for (int u = 0; u < ZU; u++) {
-        int k = k0 + u;
+        const int k = k0 + u;
         if (k < n) {
-          df d = dv[u] * scale;
+          df d = zcvt(cur[u]) * scale;
           h = (k == 0) ? d : d - wprev * h;
           wprev = W(k);
-          ZIo<S>::st(base + k * P, h);
+          zput(base + k * P, h);
         }
       }
+#pragma unroll
+      for (int u = 0; u < ZU; u++) cur[u] = nxt[u];
     }
     df x = df{0.f, 0.f};
+    zload(cur, base, P, n - 1, -1, n);
     for (int k0 = n - 1; k0 >= 0; k0 -= ZU) {
-      df hv[ZU];
-#pragma unroll
-      for (int t = 0; t < ZU; t++)
-        if (k0 - t >= 0) hv[t] = ZIo<S>::ld(base + (k0 - t) * P);
+      if (k0 - ZU >= 0) zload(nxt, base, P, k0 - ZU, -1, n);
 #pragma unroll
       for (int t = 0; t < ZU; t++) {
-        int k = k0 - t;
+        const int k = k0 - t;
         if (k >= 0) {
-          x = (k == n - 1) ? hv[t] * W(k) : (hv[t] - x) * W(k);
-          ZIo<S>::st(base + k * P, x);
+          const df hk = zcvt(cur[t]);
+          x = (k == n - 1) ? hk * W(k) : (hk - x) * W(k);
+          zput(base + k * P, x);
         }
       }
+#pragma unroll
+      for (int t = 0; t < ZU; t++) cur[t] = nxt[t];
     }
   }
 }
 
-cudaError_t launch_zsolve_impl(const ZArgs& a, bool df_spill, cudaStream_t st) {
-  int threads = 256;
-  long long grid = (a.nreal + threads - 1) / threads;
-  if (df_spill) k_zsolve<float2><<<(unsigned)grid, threads, 0, st>>>(a);
-  else k_zsolve<float><<<(unsigned)grid, threads, 0, st>>>(a);
+template <class S>
+static cudaError_t launch_z(const ZArgs& a, int mode, unsigned grid, int threads, cudaStream_t st) {
+  if (mode == 1) k_zsolve<S, 1><<<grid, threads, 0, st>>>(a);
+  else if (mode == 2) k_zsolve<S, 2><<<grid, threads, 0, st>>>(a);
+  else k_zsolve<S, 0><<<grid, threads, 0, st>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_zsolve_impl(const ZArgs& a, bool df_spill, bool zper, cudaStream_t st) {
+  const int threads = 256;
+  const long long grid = (a.nreal + threads - 1) / threads;
+  // periodic z is self-adjoint in this factorisation; the transposed sweep is for Thomas only
+  const int mode = zper ? 1 : (a.transpose ? 2 : 0);
+  return df_spill ? launch_z<float2>(a, mode, (unsigned)grid, threads, st)
+                  : launch_z<float>(a, mode, (unsigned)grid, threads, st);
 }
 
 }  // namespace pp
