@@ -189,9 +189,16 @@ __device__ __forceinline__ void fft_lines(cx<R>* buf, int nlines, int ldm, const
 // ---------------------------------------------------------------- compile-time length
 // For a power-of-two length MC known at compile time the stage sequence (radix 8 while it
 // divides, then 4, then 2) and every index division are resolved by the compiler.
+//
+// Addressing: with powers of two, pad(j + u nbl) = pad(j) + u nbl + (u nbl >> 5) and, for the
+// output position o = q + S r p (q < S), pad(o + S t) = pad(o) + S t + (S t >> 5), so every
+// shared-memory access of a butterfly is one base address plus a compile-time offset.
+// Twiddles are stored per stage in butterfly order: stage k (stride S, radix r, p < MC/(S r))
+// keeps w_MC^(p S t), t = 1..r-1, at off_k + p (r-1) + t-1; off_k = MC - MC/S (the sizes
+// telescope), and the last stage (p = 0, all twiddles 1) keeps none.
 template <int REM> struct CtRadix { static constexpr int v = (REM % 8 == 0) ? 8 : (REM % 4 == 0 ? 4 : 2); };
 
-template <class R, int RAD, bool INV, int MC, int S>
+template <class R, int RAD, bool INV, int MC, int S, int TWOFF>
 __device__ __forceinline__ void fft_stage_ct(cx<R>* buf, int nlines, int ldm, const cx<R>* tw) {
   constexpr int NB = NBut<RAD>::v;
   constexpr int nbl = MC / RAD;
@@ -199,49 +206,96 @@ __device__ __forceinline__ void fft_stage_ct(cx<R>* buf, int nlines, int ldm, co
   cx<R> a[NB][RAD];
 #pragma unroll
   for (int i = 0; i < NB; i++) {
-    int b = threadIdx.x + i * blockDim.x;
+    const int b = threadIdx.x + i * blockDim.x;
     if (b < total) {
-      int line = b / nbl, j = b % nbl;
-      const cx<R>* x = buf + line * ldm;
+      const int line = b / nbl, j = b % nbl;
+      const cx<R>* x = buf + line * ldm + pad(j);
 #pragma unroll
-      for (int u = 0; u < RAD; u++) a[i][u] = x[pad(j + u * nbl)];
+      for (int u = 0; u < RAD; u++) a[i][u] = x[u * nbl + ((u * nbl) >> 5)];
     }
   }
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < NB; i++) {
-    int b = threadIdx.x + i * blockDim.x;
+    const int b = threadIdx.x + i * blockDim.x;
     if (b < total) {
-      int line = b / nbl, j = b % nbl;
-      int p = j / S, q = j % S;
+      const int line = b / nbl, j = b % nbl;
+      const int p = j / S, q = j % S;
       dft_r<R, RAD, INV>(a[i]);
-      cx<R>* y = buf + line * ldm;
-      const int o = q + S * RAD * p;
-      y[pad(o)] = a[i][0];
+      cx<R>* y = buf + line * ldm + pad(q + S * RAD * p);
+      y[0] = a[i][0];
       if constexpr (S * RAD == MC) {
         // last stage: p = 0, every twiddle is 1
 #pragma unroll
-        for (int t = 1; t < RAD; t++) y[pad(o + S * t)] = a[i][t];
+        for (int t = 1; t < RAD; t++) y[S * t + ((S * t) >> 5)] = a[i][t];
       } else {
-        const int ps = p * S;
+        const cx<R>* w = tw + TWOFF + p * (RAD - 1);  // w[t-1] = w_MC^(p S t)
 #pragma unroll
-        for (int t = 1; t < RAD; t++) {
-          cx<R> w = tw[ps * t];
-          y[pad(o + S * t)] = INV ? cmulc(a[i][t], w) : cmul(a[i][t], w);
-        }
+        for (int t = 1; t < RAD; t++)
+          y[S * t + ((S * t) >> 5)] = INV ? cmulc(a[i][t], w[t - 1]) : cmul(a[i][t], w[t - 1]);
       }
     }
   }
   __syncthreads();
 }
 
-template <class R, bool INV, int MC, int S>
+// tw: the per-stage table of load_stage_twiddles
+template <class R, bool INV, int MC, int S, int TWOFF = 0>
 __device__ __forceinline__ void fft_lines_ct(cx<R>* buf, int nlines, int ldm, const cx<R>* tw) {
   if constexpr (S < MC) {
     constexpr int RAD = CtRadix<MC / S>::v;
-    fft_stage_ct<R, RAD, INV, MC, S>(buf, nlines, ldm, tw);
-    fft_lines_ct<R, INV, MC, S * RAD>(buf, nlines, ldm, tw);
+    fft_stage_ct<R, RAD, INV, MC, S, TWOFF>(buf, nlines, ldm, tw);
+    constexpr int NEXT = (S * RAD < MC) ? TWOFF + (MC / (S * RAD)) * (RAD - 1) : TWOFF;
+    fft_lines_ct<R, INV, MC, S * RAD, NEXT>(buf, nlines, ldm, tw);
   }
+}
+
+// Radix-8 stage with the stride S = 2^lgS known only at run time (one butterfly per thread).  The
+// double-float butterfly is long (~900 instructions); running all radix-8 stages through one copy
+// of it keeps the kernel's hot code within the instruction cache.  Same addressing and twiddle
+// table as fft_stage_ct (radix-8 stages come first, so this stage's twiddles start at MC - MC/S).
+template <class R, bool INV, int MC>
+__device__ __forceinline__ void fft_stage8_rt(cx<R>* buf, int nlines, int ldm, const cx<R>* tw, int lgS, bool last) {
+  constexpr int nbl = MC / 8;
+  const int total = nlines * nbl;
+  const int b = threadIdx.x;
+  const int line = b / nbl, j = b % nbl;
+  cx<R> a[8];
+  const bool act = b < total;
+  if (act) {
+    const cx<R>* x = buf + line * ldm + pad(j);
+#pragma unroll
+    for (int u = 0; u < 8; u++) a[u] = x[u * nbl + ((u * nbl) >> 5)];
+  }
+  __syncthreads();
+  if (act) {
+    const int p = j >> lgS, q = j & ((1 << lgS) - 1);
+    dft8<R, INV>(a);
+    cx<R>* y = buf + line * ldm + pad(q + ((8 * p) << lgS));
+    y[0] = a[0];
+    if (last) {
+#pragma unroll
+      for (int t = 1; t < 8; t++) y[(t << lgS) + ((t << lgS) >> 5)] = a[t];
+    } else {
+      const cx<R>* w = tw + (MC - (MC >> lgS)) + p * 7;
+#pragma unroll
+      for (int t = 1; t < 8; t++)
+        y[(t << lgS) + ((t << lgS) >> 5)] = INV ? cmulc(a[t], w[t - 1]) : cmul(a[t], w[t - 1]);
+    }
+  }
+  __syncthreads();
+}
+
+// All stages of a power-of-two length: the radix-8 stages in a loop (not unrolled), then the
+// remaining radix-4 or radix-2 stage.  Same stage sequence and results as fft_lines_ct.
+template <class R, bool INV, int MC>
+__device__ __forceinline__ void fft_lines_lp(cx<R>* buf, int nlines, int ldm, const cx<R>* tw) {
+  constexpr int L8 = (MC >= 8) ? (31 - __builtin_clz(MC)) / 3 : 0;
+  constexpr int REM = MC >> (3 * L8);
+#pragma unroll 1
+  for (int st = 0; st < L8; st++) fft_stage8_rt<R, INV, MC>(buf, nlines, ldm, tw, 3 * st, REM == 1 && st == L8 - 1);
+  if constexpr (REM == 4) fft_stage_ct<R, 4, INV, MC, MC / 4, 0>(buf, nlines, ldm, tw);
+  if constexpr (REM == 2) fft_stage_ct<R, 2, INV, MC, MC / 2, 0>(buf, nlines, ldm, tw);
 }
 
 }  // namespace pp

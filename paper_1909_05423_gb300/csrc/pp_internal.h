@@ -59,6 +59,11 @@ struct LineArgs {
 };
 constexpr int kMaxLpc = 512;  // lines per CTA (bounded so the per-line bases fit in shared memory)
 
+// Complex FFT lengths with kernels compiled for the length: powers of two 64..1024.  Their stage
+// twiddles are stored per stage in butterfly order (fft_lines_ct); other lengths keep w_M^j, j < M.
+constexpr int kCtMin = 64, kCtMax = 1024;
+inline bool ct_length(int M) { return M >= kCtMin && M <= kCtMax && (M & (M - 1)) == 0; }
+
 // Per-mode z-solve descriptor (tables computed on the host in FP64).
 struct ZMode {
   int woff, wlen;     // prefix of Thomas multipliers w_k in the w table

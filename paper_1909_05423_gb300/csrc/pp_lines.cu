@@ -10,7 +10,7 @@ cudaError_t launch_lines_impl(const LineArgs& a, bool df_arith, int oy, int sin,
   (void)smem;
   (void)grid;
   const int M = a.fp.M;
-  const bool small = (M == 64 || M == 128 || M == 256), large = (M == 512 || M == 1024);
+  const bool small = ct_length(M) && M <= 256, large = ct_length(M) && M >= 512;
   if (df_arith) {
     if (small) return lines_df_small(a, oy, sin, sout, threads, st);
     if (large) return lines_df_large(a, oy, sin, sout, threads, st);

@@ -614,6 +614,7 @@ __global__ void __launch_bounds__(512, MinBlocks<R>::v) k_lines(const LineArgs a
   cx<R>* buf = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* tws = buf + (size_t)a.lpc * ldm;
   const cx<R>* twg = reinterpret_cast<const cx<R>*>(a.tw);
+  // stage twiddles: w_M^j, j < M (run-time lengths) or the per-stage table of fft_lines_ct
   for (int i = threadIdx.x; i < M; i += blockDim.x) tws[i] = twg[i];
   const int kind = a.kind;
   const bool inv = (kind == LK_C2R || kind == LK_C2C_I || kind == LK_DCT3 || kind == LK_DST3);
@@ -636,8 +637,15 @@ __global__ void __launch_bounds__(512, MinBlocks<R>::v) k_lines(const LineArgs a
   pre_tile<R, OY, MC>(a, SrcGlobal<R, SI>{reinterpret_cast<const SI*>(a.in), s_bin, (long long)a.in_pos}, nl, buf);
   __syncthreads();
   if constexpr (MC > 0) {
-    if (inv) fft_lines_ct<R, true, MC, 1>(buf, nl, ldm, tws);
-    else fft_lines_ct<R, false, MC, 1>(buf, nl, ldm, tws);
+    // double-float lines of 512+ complex points: radix-8 stages share one copy of the butterfly
+    // (measured faster there; the shorter lengths keep fully compile-time stages)
+    if constexpr (std::is_same<R, df>::value && MC >= 512) {
+      if (inv) fft_lines_lp<R, true, MC>(buf, nl, ldm, tws);
+      else fft_lines_lp<R, false, MC>(buf, nl, ldm, tws);
+    } else {
+      if (inv) fft_lines_ct<R, true, MC, 1>(buf, nl, ldm, tws);
+      else fft_lines_ct<R, false, MC, 1>(buf, nl, ldm, tws);
+    }
   } else {
     if (inv) fft_lines<R, true>(buf, nl, ldm, a.fp, tws);
     else fft_lines<R, false>(buf, nl, ldm, a.fp, tws);

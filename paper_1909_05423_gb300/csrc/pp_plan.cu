@@ -188,7 +188,21 @@ static pp_status axis_tables(pp_plan* p, int ax, int N, bool complex_data, FftPl
   fp = make_fft(M);
   Tab tw{{}, dfm}, aux{{}, dfm};
   double re, im;
-  for (int j = 0; j < M; j++) { expi(j, M, re, im); tw.push(re, im); }
+  if (ct_length(M)) {
+    // per-stage table in butterfly order: stage (stride S, radix r), p < M/(S r), t = 1..r-1 holds
+    // w_M^(p S t); the last stage has no twiddles (the sizes telescope to M - 1 entries at most)
+    int S = 1;
+    for (int st = 0; st < fp.nst; st++) {
+      const int r = fp.rad[st];
+      if (S * r < M)
+        for (int p = 0; p < M / (S * r); p++)
+          for (int t = 1; t < r; t++) { expi((long long)p * S * t, M, re, im); tw.push(re, im); }
+      S *= r;
+    }
+    while ((int)(tw.v.size() / (dfm ? 4 : 2)) < M) tw.push(0.0, 0.0);  // the kernels copy M entries
+  } else {
+    for (int j = 0; j < M; j++) { expi(j, M, re, im); tw.push(re, im); }
+  }
   if (ax == AX_P && !complex_data) {
     for (int k = 0; k <= M; k++) { expi(k, N, re, im); aux.push(re, im); }
   } else if (ax == AX_NN || ax == AX_DD) {
