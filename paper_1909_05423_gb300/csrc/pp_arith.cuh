@@ -5,9 +5,10 @@
 // "double-float" arithmetic: a value is an unevaluated sum hi + lo of two FP32
 // numbers (Dekker 1971, "A floating-point technique for extending the available
 // precision"; Knuth's TwoSum), giving a ~47-bit significand.  FP64 grid values
-// are split into (hi, lo) and re-assembled with integer bit operations, which
-// run at full rate.  The mixed-precision path uses plain FP32 for the
-// transforms and the same double-float arithmetic in the tridiagonal solve.
+// are split into (hi, lo) with integer bit operations and re-assembled with one
+// FP64 add of the two exactly converted parts.  The mixed-precision path uses
+// plain FP32 for the transforms and the same double-float arithmetic in the
+// tridiagonal solve.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -84,9 +85,14 @@ __device__ __forceinline__ df df_rcp(df a) {
 }
 
 // ------------------------------------------------ FP64 <-> double-float (integer)
-// Split an FP64 value into hi + lo (hi = truncated 24-bit significand, lo = the next 23 bits),
-// using integer operations only.  |d| < 2^-103 keeps only hi; |d| < 2^-126 flushes to zero.
-__device__ __forceinline__ df df_from_double(double d) {
+// Integer instructions run at half the FP32 rate on this GPU, so each conversion has a short
+// path for the normal range (one range test) and falls back to the general code otherwise.
+// t = |high word| - (896 << 20) re-biases the FP64 exponent to FP32: for 1 <= e_f <= 254,
+// t = e_f 2^20 + (top 20 mantissa bits), and (t << 3) | (low word >> 29) is the FP32 magnitude
+// truncated to 23 mantissa bits.
+
+// General-case split (every exponent, inf, nan); see df_from_double.
+static __device__ __noinline__ df df_from_double_slow(double d) {
   unsigned long long b = (unsigned long long)__double_as_longlong(d);
   unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
   unsigned sign = h32 & 0x80000000u;
@@ -110,31 +116,46 @@ __device__ __forceinline__ df df_from_double(double d) {
   return r;
 }
 
-// Assemble hi + lo into the FP64 value (truncated to 53 bits), integer operations only.
-__device__ __forceinline__ double df_to_double(df v) {
-  unsigned hb = __float_as_uint(v.hi), lb = __float_as_uint(v.lo);
-  int eh = (int)((hb >> 23) & 0xffu);
-  unsigned long long sign = (unsigned long long)(hb & 0x80000000u) << 32;
-  if (eh == 0) return __longlong_as_double((long long)sign);
-  if (eh == 255) return __longlong_as_double((long long)(sign | 0x7ff0000000000000ull |
-                                                          ((hb & 0x7fffffu) ? 0x8000000000000ull : 0ull)));
-  long long X = (long long)(((unsigned long long)((hb & 0x7fffffu) | 0x800000u)) << 29);
-  int el = (int)((lb >> 23) & 0xffu);
-  if (el != 0) {
-    long long Ml = (long long)((lb & 0x7fffffu) | 0x800000u);
-    int sh = (eh - el) - 29;  // right shift of lo's 24-bit significand into units of 2^(eh-127-52)
-    long long L = (sh <= 0) ? (Ml << (-sh < 40 ? -sh : 40)) : (sh < 40 ? (Ml >> sh) : 0);
-    X = ((hb ^ lb) & 0x80000000u) ? X - L : X + L;
-  }
-  int e = eh - 127 + 1023;
-  if (X >= (1LL << 53)) { X >>= 1; e += 1; }
-  else if (X < (1LL << 52)) { X <<= 1; e -= 1; }
-  unsigned long long bits = sign | ((unsigned long long)e << 52) | ((unsigned long long)X & 0xfffffffffffffull);
-  return __longlong_as_double((long long)bits);
+// Split an FP64 value into hi + lo (hi = truncated 24-bit significand, lo = the next 23 bits),
+// using integer operations only.  |d| < 2^-103 keeps only hi; |d| < 2^-126 flushes to zero.
+__device__ __forceinline__ df df_from_double(double d) {
+  const unsigned h32 = (unsigned)__double2hiint(d), l32 = (unsigned)__double2loint(d);
+  const unsigned sign = h32 & 0x80000000u;
+  const unsigned t = (h32 & 0x7fffffffu) - (896u << 20);
+  if (t - (24u << 20) >= (231u << 20)) return df_from_double_slow(d);  // e_f outside [24, 254]
+  df r;
+  r.hi = __uint_as_float(sign | __funnelshift_l(l32, t, 3));
+  // lo: the 23 bits below hi's last place, as (2^(e_f-23) (1 + m/2^23)) - 2^(e_f-23)
+  const unsigned base = sign | ((t - (23u << 20)) >> 20 << 23);
+  r.lo = __fsub_rn(__uint_as_float(base | ((l32 & 0x1fffffffu) >> 6)), __uint_as_float(base));
+  return r;
 }
 
-// FP64 -> FP32 rounded to nearest (ties away), integer operations only.
-__device__ __forceinline__ float f32_from_double(double d) {
+// FP32 -> FP64, exact, integer operations only.
+__device__ __forceinline__ double double_from_f32(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned a = u & 0x7fffffffu;
+  if (a - 0x00800000u < 0x7f000000u)  // normal: 1 <= e_f <= 254
+    return __hiloint2double((int)((u & 0x80000000u) | ((a >> 3) + (896u << 20))), (int)(u << 29));
+  unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  if (a == 0) return __longlong_as_double((long long)sign);
+  if (a < 0x00800000u) {
+    // subnormal a 2^-149: shift the leading one to bit 23; the exponent drops by the shift
+    const int sh = __clz((int)a) - 8;
+    const unsigned m = (a << sh) & 0x7fffffu;
+    return __longlong_as_double((long long)(sign | ((unsigned long long)(897 - sh) << 52) | ((unsigned long long)m << 29)));
+  }
+  return __longlong_as_double((long long)(sign | 0x7ff0000000000000ull | ((u & 0x7fffffu) ? 0x8000000000000ull : 0ull)));
+}
+
+// hi + lo as the nearest FP64 value: both parts are exact in FP64, one FP64 add (the FP64 unit
+// runs beside the FP32 and integer pipes, and one add per value costs it little).
+__device__ __forceinline__ double df_to_double(df v) {
+  return __dadd_rn(double_from_f32(v.hi), double_from_f32(v.lo));
+}
+
+// General-case FP64 -> FP32; see f32_from_double.
+static __device__ __noinline__ float f32_from_double_slow(double d) {
   unsigned long long b = (unsigned long long)__double_as_longlong(d);
   unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
   unsigned sign = h32 & 0x80000000u;
@@ -148,16 +169,14 @@ __device__ __forceinline__ float f32_from_double(double d) {
   return __uint_as_float(sign | mag);
 }
 
-// FP32 -> FP64, exact, integer operations only (denormal floats flush to zero).
-__device__ __forceinline__ double double_from_f32(float f) {
-  unsigned u = __float_as_uint(f);
-  unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
-  unsigned ef = (u >> 23) & 0xffu;
-  if (ef == 0) return __longlong_as_double((long long)sign);
-  if (ef == 255) return __longlong_as_double((long long)(sign | 0x7ff0000000000000ull |
-                                                          ((u & 0x7fffffu) ? 0x8000000000000ull : 0ull)));
-  unsigned long long bits = sign | ((unsigned long long)(ef + 896) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
-  return __longlong_as_double((long long)bits);
+// FP64 -> FP32 rounded to nearest (ties away), integer operations only.
+__device__ __forceinline__ float f32_from_double(double d) {
+  const unsigned h32 = (unsigned)__double2hiint(d), l32 = (unsigned)__double2loint(d);
+  const unsigned t = (h32 & 0x7fffffffu) - (896u << 20);
+  if (t - (1u << 20) >= (254u << 20)) return f32_from_double_slow(d);  // e_f outside [1, 254]
+  // rounding carries propagate into the exponent (254 with all ones rounds to inf, as it should)
+  const unsigned mag = __funnelshift_l(l32, t, 3) + ((l32 >> 28) & 1u);
+  return __uint_as_float((h32 & 0x80000000u) | mag);
 }
 
 __device__ __forceinline__ float df_to_f32(df v) { return __fadd_rn(v.hi, v.lo); }
