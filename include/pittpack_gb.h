@@ -72,10 +72,15 @@ typedef struct pp_plan_options {
   int threads_y;   /* CTA size of the y-line kernels (0 = automatic) */
   int lines_x;     /* lines per CTA, x kernels (0 = automatic) */
   int cols_y;      /* columns per CTA, y kernels (0 = automatic) */
-  int autotune;    /* 1: time candidate CTA sizes / lines per CTA for the x and y kernels at plan
-                      creation and keep the fastest (results cached per device, sizes, boundary
-                      set and dtype for the life of the process); 0: fixed heuristics */
-  int reserved[7]; /* must be zero */
+  int autotune;    /* 1: time candidate CTA sizes / lines per CTA for each of the four line
+                      kernels at plan creation and keep the fastest (results cached per device,
+                      sizes, boundary set and dtype for the life of the process); 0: fixed
+                      heuristics */
+  int threads_x_inv; /* the same four settings for the inverse-transform kernels */
+  int lines_x_inv;   /*   (0 = as the forward setting above)                      */
+  int threads_y_inv;
+  int cols_y_inv;
+  int reserved[3]; /* must be zero */
 } pp_plan_options;
 
 typedef struct pp_plan pp_plan;

@@ -32,7 +32,9 @@ class PPError(RuntimeError):
 
 class PlanOptions(ctypes.Structure):
     _fields_ = [("threads_x", ctypes.c_int), ("threads_y", ctypes.c_int), ("lines_x", ctypes.c_int),
-                ("cols_y", ctypes.c_int), ("autotune", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("cols_y", ctypes.c_int), ("autotune", ctypes.c_int), ("threads_x_inv", ctypes.c_int),
+                ("lines_x_inv", ctypes.c_int), ("threads_y_inv", ctypes.c_int), ("cols_y_inv", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
 
 
 _lock = threading.Lock()

@@ -123,8 +123,8 @@ struct pp_plan {
   long long nmodes;
   double zscale;
   // launch shapes
-  int threads_x, lpc_x, ldm_x;
-  int threads_y, lpc_y, ldm_y;
+  int threads_x[2], lpc_x[2], ldm_x;  // [0] forward, [1] inverse kernels
+  int threads_y[2], lpc_y[2], ldm_y;
   // mixed-precision refinement scratch
   void* d_resid;       // residual / correction (FP64 I/O size)
   void* d_mean;        // kMeanParts partial sums + 1 mean (float2 each), singular refinement
@@ -140,6 +140,8 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
 cudaError_t launch_zsolve(const pp_plan* p, void* data, int transpose, cudaStream_t st);
 cudaError_t launch_residual(const pp_plan* p, const void* f, const void* u, void* r, cudaStream_t st);
 cudaError_t launch_add(const pp_plan* p, void* u, const void* d, const void* shift, cudaStream_t st);
+// n pseudo-random values in [-1, 1) (FP32 or FP64), timing input of the autotuner
+cudaError_t launch_fill(void* x, long long n, bool f32, cudaStream_t st);
 // mean of an FP64 grid: nparts block sums into `partials` (nparts float2), result (hi,lo) into `mean`
 cudaError_t launch_mean(const pp_plan* p, const void* u, void* partials, int nparts, void* mean, cudaStream_t st);
 constexpr int kMeanParts = 1024;

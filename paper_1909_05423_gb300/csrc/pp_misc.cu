@@ -122,6 +122,25 @@ cudaError_t launch_mean(const pp_plan* p, const void* u, void* partials, int npa
   return cudaGetLastError();
 }
 
+// Timing input of the autotuner: values in [-1, 1) from an integer hash of the index (no
+// statistical quality needed, only normal non-constant data).
+__global__ void k_fill(void* x, long long n, int f32) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  unsigned h = (unsigned)i * 2654435761u;
+  h ^= h >> 15;
+  h *= 2246822519u;
+  h ^= h >> 13;
+  const float v = (float)(h >> 8) * (1.0f / 8388608.0f) - 1.0f;
+  if (f32) reinterpret_cast<float*>(x)[i] = v;
+  else reinterpret_cast<double*>(x)[i] = double_from_f32(v);
+}
+
+cudaError_t launch_fill(void* x, long long n, bool f32, cudaStream_t st) {
+  k_fill<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, n, f32 ? 1 : 0);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_add(const pp_plan* p, void* u, const void* d, const void* shift, cudaStream_t st) {
   long long n = (long long)p->nx * p->ny * p->nz;
   k_add<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((double*)u, (const double*)d, n, (const float2*)shift);

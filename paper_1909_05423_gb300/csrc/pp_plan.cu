@@ -360,68 +360,79 @@ static void free_plan(pp_plan* p) {
   delete p;
 }
 
-// launch shapes: threads per CTA and lines per CTA of the x and y line kernels.  Shared memory
-// per CTA = the complex work buffer + the stage twiddles.
+// launch shapes: threads per CTA and lines per CTA of the x and y line kernels, per direction
+// (0 forward, 1 inverse).  Shared memory per CTA = the complex work buffer + the stage twiddles.
 static void choose_shapes(pp_plan* p, const pp_plan_options* opt) {
   size_t cs = (p->dtype == PP_F64) ? 16 : 8;          // bytes per complex in shared memory
   size_t se = p->elem;                                  // bytes per spill real
   const size_t smem_cap = 200 * 1024;
-  // x lines: a staged tile holds lpc rows of the wider of (grid row, spectral row)
-  {
-    int M = p->fx.M;
-    bool r3 = false;
-    for (int i = 0; i < p->fx.nst; i++) r3 |= p->fx.rad[i] == 3;
-    // a CTA must hold at least one whole line: threads * kCapPerThread >= M
-    const int tmin = std::max(32, ((M + kCapPerThread - 1) / kCapPerThread + 31) / 32 * 32);
-    int T = (opt && opt->threads_x) ? opt->threads_x : 128;
-    T = std::max(T, tmin);
-    int cap = (r3 ? kCapPerThread3 : kCapPerThread) * T;
-    int nlines = p->ny * p->nz;
-    int lpc = std::max(1, cap / std::max(M, 1));
-    if (opt && opt->lines_x) lpc = std::min(lpc, opt->lines_x);
-    lpc = std::min(lpc, kMaxLpc);
-    lpc = std::min(lpc, nlines);
-    int ldm = M + (M >> 5) + 1;  // one padding slot per 32 elements (see pad() in pp_fft.cuh)
-    auto need = [&](int l) { return (size_t)l * ldm * cs + (size_t)M * cs; };
-    while (lpc > 1 && need(lpc) > smem_cap) lpc--;
-    p->threads_x = T;
-    p->lpc_x = lpc;
-    p->ldm_x = ldm;
-  }
-  // y lines: a staged tile holds up to ny rows of tx columns
-  {
-    int M = p->fy.M;
-    bool r3 = false;
-    for (int i = 0; i < p->fy.nst; i++) r3 |= p->fy.rad[i] == 3;
-    bool cplx_cols = (p->layout == 0);
-    int parts = (cplx_cols && p->ky != AX_P) ? 2 : 1;
-    int ncols = cplx_cols ? p->nx / 2 + 1 : p->nx;
-    size_t col_bytes = (cplx_cols ? 2 : 1) * se;
-    // CTA size: 128 threads unless that leaves column segments below one 32-byte sector
-    const int tmin = std::max(32, ((M + kCapPerThread - 1) / kCapPerThread + 31) / 32 * 32);
-    int T = 128;
-    const int tmax = 512;
-    if (opt && opt->threads_y) T = opt->threads_y;
-    else
-      while (T < tmax && (size_t)std::max(1, (kCapPerThread3 * T / std::max(M, 1)) / parts) * col_bytes < 32) T *= 2;
-    T = std::max(T, tmin);
-    int cap = (r3 ? kCapPerThread3 : kCapPerThread) * T;
-    int maxlines = std::max(1, cap / std::max(M, 1));
-    int cols = std::max(1, maxlines / parts);
-    if (opt && opt->cols_y) cols = std::min(cols, opt->cols_y);
-    cols = std::min(cols, kMaxLpc / parts);
-    cols = std::min(cols, ncols);
-    // complex columns split into two real lines need room for both
-    while (cols * parts * M > cap && T < tmax) {
-      T = std::min(2 * T, tmax);
-      cap = (r3 ? kCapPerThread3 : kCapPerThread) * T;
+  for (int dir = 0; dir < 2; dir++) {
+    // requested settings of this direction (the inverse ones default to the forward ones)
+    int tx_req = opt ? opt->threads_x : 0, lx_req = opt ? opt->lines_x : 0;
+    int ty_req = opt ? opt->threads_y : 0, cy_req = opt ? opt->cols_y : 0;
+    if (dir == 1 && opt) {
+      if (opt->threads_x_inv) tx_req = opt->threads_x_inv;
+      if (opt->lines_x_inv) lx_req = opt->lines_x_inv;
+      if (opt->threads_y_inv) ty_req = opt->threads_y_inv;
+      if (opt->cols_y_inv) cy_req = opt->cols_y_inv;
     }
-    int ldm = M + (M >> 5) + 1;
-    auto need = [&](int c) { return (size_t)c * parts * ldm * cs + (size_t)M * cs; };
-    while (cols > 1 && need(cols) > smem_cap) cols--;
-    p->threads_y = T;
-    p->lpc_y = cols * parts;
-    p->ldm_y = ldm;
+    // x lines: a staged tile holds lpc rows of the wider of (grid row, spectral row)
+    {
+      int M = p->fx.M;
+      bool r3 = false;
+      for (int i = 0; i < p->fx.nst; i++) r3 |= p->fx.rad[i] == 3;
+      // a CTA must hold at least one whole line: threads * kCapPerThread >= M
+      const int tmin = std::max(32, ((M + kCapPerThread - 1) / kCapPerThread + 31) / 32 * 32);
+      int T = tx_req ? tx_req : 128;
+      T = std::max(T, tmin);
+      int cap = (r3 ? kCapPerThread3 : kCapPerThread) * T;
+      int nlines = p->ny * p->nz;
+      int lpc = std::max(1, cap / std::max(M, 1));
+      if (lx_req) lpc = std::min(lpc, lx_req);
+      lpc = std::min(lpc, kMaxLpc);
+      lpc = std::min(lpc, nlines);
+      int ldm = M + (M >> 5) + 1;  // one padding slot per 32 elements (see pad() in pp_fft.cuh)
+      auto need = [&](int l) { return (size_t)l * ldm * cs + (size_t)M * cs; };
+      while (lpc > 1 && need(lpc) > smem_cap) lpc--;
+      p->threads_x[dir] = T;
+      p->lpc_x[dir] = lpc;
+      p->ldm_x = ldm;
+    }
+    // y lines: a staged tile holds up to ny rows of tx columns
+    {
+      int M = p->fy.M;
+      bool r3 = false;
+      for (int i = 0; i < p->fy.nst; i++) r3 |= p->fy.rad[i] == 3;
+      bool cplx_cols = (p->layout == 0);
+      int parts = (cplx_cols && p->ky != AX_P) ? 2 : 1;
+      int ncols = cplx_cols ? p->nx / 2 + 1 : p->nx;
+      size_t col_bytes = (cplx_cols ? 2 : 1) * se;
+      // CTA size: 128 threads unless that leaves column segments below one 32-byte sector
+      const int tmin = std::max(32, ((M + kCapPerThread - 1) / kCapPerThread + 31) / 32 * 32);
+      int T = 128;
+      const int tmax = 512;
+      if (ty_req) T = ty_req;
+      else
+        while (T < tmax && (size_t)std::max(1, (kCapPerThread3 * T / std::max(M, 1)) / parts) * col_bytes < 32) T *= 2;
+      T = std::max(T, tmin);
+      int cap = (r3 ? kCapPerThread3 : kCapPerThread) * T;
+      int maxlines = std::max(1, cap / std::max(M, 1));
+      int cols = std::max(1, maxlines / parts);
+      if (cy_req) cols = std::min(cols, cy_req);
+      cols = std::min(cols, kMaxLpc / parts);
+      cols = std::min(cols, ncols);
+      // complex columns split into two real lines need room for both
+      while (cols * parts * M > cap && T < tmax) {
+        T = std::min(2 * T, tmax);
+        cap = (r3 ? kCapPerThread3 : kCapPerThread) * T;
+      }
+      int ldm = M + (M >> 5) + 1;
+      auto need = [&](int c) { return (size_t)c * parts * ldm * cs + (size_t)M * cs; };
+      while (cols > 1 && need(cols) > smem_cap) cols--;
+      p->threads_y[dir] = T;
+      p->lpc_y[dir] = cols * parts;
+      p->ldm_y = ldm;
+    }
   }
 }
 
@@ -462,7 +473,7 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
     a.nlines = p->ny * p->nz;
     a.lines_per_plane = p->ny;
     a.parts = 1;
-    a.lpc = p->lpc_x;
+    a.lpc = p->lpc_x[dir];
     a.ldm = p->ldm_x;
     a.fp = p->fx;
     a.tw = p->d_tw_x;
@@ -476,12 +487,12 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
       a.in_plane = sp_plane; a.in_line = (int)sp_row; a.in_pos = per ? 2 : 1;
       a.out_plane = grid_plane; a.out_line = grid_row; a.out_pos = 1;
     }
-    if ((long long)a.lpc * a.fp.M > (long long)kCapPerThread * p->threads_x) return cudaErrorInvalidConfiguration;
+    if ((long long)a.lpc * a.fp.M > (long long)kCapPerThread * p->threads_x[dir]) return cudaErrorInvalidConfiguration;
     a.ntiles = (a.nlines + a.lpc - 1) / a.lpc;
     a.vec_ok = (((uintptr_t)in | (uintptr_t)out) % 32 == 0) ? 1 : 0;
     a.fd_gpc = FastDiv::make(1u);
     finish_args(a);
-    return launch_lines_impl(a, dfm, 0, io_in, io_out, p->threads_x, 0, 0, st);
+    return launch_lines_impl(a, dfm, 0, io_in, io_out, p->threads_x[dir], 0, 0, st);
   }
   // y
   const bool cplx_cols = (p->layout == 0);
@@ -492,7 +503,7 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
   a.parts = parts;
   a.lines_per_plane = ncols * parts;
   a.nlines = a.lines_per_plane * p->nz;
-  a.lpc = p->lpc_y;
+  a.lpc = p->lpc_y[dir];
   a.ldm = p->ldm_y;
   a.fp = p->fy;
   a.tw = p->d_tw_y;
@@ -510,7 +521,7 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
     a.in_plane = s_plane; a.in_line = (int)s_col; a.in_pos = (int)s_pos;
     a.out_plane = xs_plane; a.out_line = xs_col; a.out_pos = xs_pos;
   }
-  if ((long long)a.lpc * a.fp.M > (long long)kCapPerThread * p->threads_y) return cudaErrorInvalidConfiguration;
+  if ((long long)a.lpc * a.fp.M > (long long)kCapPerThread * p->threads_y[dir]) return cudaErrorInvalidConfiguration;
   a.tx = a.lpc / parts;
   a.ncols = ncols;
   a.nblk = (ncols + a.tx - 1) / a.tx;
@@ -528,7 +539,7 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
   }
   finish_args(a);
   a.fd_nblk = FastDiv::make((unsigned)a.nblk);
-  return launch_lines_impl(a, dfm, 1, io_in, io_out, p->threads_y, 0, 0, st);
+  return launch_lines_impl(a, dfm, 1, io_in, io_out, p->threads_y[dir], 0, 0, st);
 }
 
 cudaError_t launch_zsolve(const pp_plan* p, void* data, int transpose, cudaStream_t st) {
@@ -609,10 +620,9 @@ static pp_status autotune(pp_plan* p) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t ce = cudaMalloc(&f, bytes);
   if (ce == cudaSuccess) ce = cudaMalloc(&u, bytes);
-  // timing input: every byte 0x3f is a normal FP64 (and FP32) value, so the conversions and
-  // transforms take their usual paths (zeros would take the special-value ones)
-  if (ce == cudaSuccess) ce = cudaMemset(f, 0x3f, bytes);
   if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  // timing input: non-constant normal values, so conversions and transforms take their usual paths
+  if (ce == cudaSuccess) ce = launch_fill(f, (long long)p->nx * p->ny * p->nz, io == 4, st);
   if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
   if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
   auto cleanup = [&]() {
@@ -623,12 +633,12 @@ static pp_status autotune(pp_plan* p) {
     if (e1) cudaEventDestroy(e1);
   };
   if (ce != cudaSuccess) { cleanup(); return fail(PP_ERR_OUT_OF_MEMORY, "autotune scratch: %s", cudaGetErrorString(ce)); }
-  // time stages s0, s1 (3 runs after one warm-up), in ms; +inf on a failed launch
-  auto time_pair = [&](int s0, int s1) -> float {
+  // time one stage (3 runs after one warm-up), in ms; +inf on a failed launch
+  auto time_stage = [&](int s0) -> float {
     float best = 1e30f;
     for (int r = 0; r < 4; r++) {
       cudaEventRecord(e0, st);
-      if (run_stage(p, s0, f, u, 0, st) != PP_OK || run_stage(p, s1, f, u, 0, st) != PP_OK) return 1e30f;
+      if (run_stage(p, s0, f, u, 0, st) != PP_OK) return 1e30f;
       cudaEventRecord(e1, st);
       if (cudaEventSynchronize(e1) != cudaSuccess) return 1e30f;
       float ms = 0.f;
@@ -637,48 +647,46 @@ static pp_status autotune(pp_plan* p) {
     }
     return best;
   };
-  const int tmax = 512;
   const int tcand[] = {64, 128, 256, 512};
   pp_plan_options best;
   memset(&best, 0, sizeof best);
-  // x kernels
-  float bx = 1e30f;
-  for (int T : tcand) {
-    if (T > tmax) continue;
-    for (int half = 0; half < 2; half++) {
-      pp_plan_options o;
-      memset(&o, 0, sizeof o);
-      o.threads_x = T;
-      choose_shapes(p, &o);
-      if (half) {
-        if (p->lpc_x < 2) continue;
-        o.lines_x = p->lpc_x / 2;
+  // Each line stage is tuned on its own, in pipeline order, so that every stage reads the output
+  // of the previous one: x-forward, y-forward, (z), y-inverse, x-inverse.  Candidates: CTA sizes
+  // x {as many lines as fit, half of them}.
+  float bt[4] = {1e30f, 1e30f, 1e30f, 1e30f};
+  const int stages[4] = {0, 1, 3, 4};
+  for (int si = 0; si < 4; si++) {
+    const int stage = stages[si];
+    const bool xa = (stage == 0 || stage == 4), inv = (stage >= 3);
+    if (stage == 3 && run_stage(p, 2, f, u, 0, st) != PP_OK) break;  // z solve between the y stages
+    for (int T : tcand) {
+      for (int half = 0; half < 2; half++) {
+        pp_plan_options o = best;
+        int* tr = xa ? (inv ? &o.threads_x_inv : &o.threads_x) : (inv ? &o.threads_y_inv : &o.threads_y);
+        int* lr = xa ? (inv ? &o.lines_x_inv : &o.lines_x) : (inv ? &o.cols_y_inv : &o.cols_y);
+        *tr = T;
+        *lr = 0;
         choose_shapes(p, &o);
+        if (half) {
+          const int parts = (!xa && p->layout == 0 && p->ky != AX_P) ? 2 : 1;
+          const int have = (xa ? p->lpc_x[inv] : p->lpc_y[inv]) / parts;
+          if (have < 2) continue;
+          *lr = have / 2;
+          choose_shapes(p, &o);
+        }
+        const float t = time_stage(stage);
+        if (t < bt[si]) {
+          bt[si] = t;
+          const int* got = xa ? p->threads_x : p->threads_y;
+          if (xa) { if (inv) { best.threads_x_inv = got[1]; best.lines_x_inv = o.lines_x_inv; } else { best.threads_x = got[0]; best.lines_x = o.lines_x; } }
+          else { if (inv) { best.threads_y_inv = got[1]; best.cols_y_inv = o.cols_y_inv; } else { best.threads_y = got[0]; best.cols_y = o.cols_y; } }
+        }
       }
-      float t = time_pair(0, 4);
-      if (t < bx) { bx = t; best.threads_x = p->threads_x; best.lines_x = o.lines_x; }
     }
+    choose_shapes(p, &best);
+    if (run_stage(p, stage, f, u, 0, st) != PP_OK) break;  // leave this stage's output for the next one
   }
-  // y kernels (x part fixed at its best)
-  float by = 1e30f;
-  for (int T : tcand) {
-    if (T > tmax) continue;
-    for (int half = 0; half < 2; half++) {
-      pp_plan_options o = best;
-      o.threads_y = T;
-      o.cols_y = 0;
-      choose_shapes(p, &o);
-      if (half) {
-        int parts = (p->layout == 0 && p->ky != AX_P) ? 2 : 1;
-        int cols = p->lpc_y / parts;
-        if (cols < 2) continue;
-        o.cols_y = cols / 2;
-        choose_shapes(p, &o);
-      }
-      float t = time_pair(1, 3);
-      if (t < by) { by = t; best.threads_y = p->threads_y; best.cols_y = o.cols_y; }
-    }
-  }
+  const float bx = std::max(bt[0], bt[3]), by = std::max(bt[1], bt[2]);
   cleanup();
   if (bx >= 1e30f || by >= 1e30f) return fail(PP_ERR_CUDA, "autotune: no candidate launch shape ran");
   choose_shapes(p, &best);
@@ -745,13 +753,16 @@ pp_status pp_plan_create(pp_plan** out, int nx, int ny, int nz, const pp_bc bc[6
     if ((bc[2 * a] == PP_BC_PERIODIC) != (bc[2 * a + 1] == PP_BC_PERIODIC))
       return fail(PP_ERR_BC_PAIRING, "axis %d: periodic must be given on both faces", a);
   if (opt)
-    for (int i = 0; i < 7; i++)
+    for (int i = 0; i < 3; i++)
       if (opt->reserved[i]) return fail(PP_ERR_INVALID_ARG, "options.reserved must be zero");
   const int tmax = 512;
-  if (opt && (opt->threads_x < 0 || opt->threads_y < 0 || opt->lines_x < 0 || opt->cols_y < 0 ||
-              (opt->threads_x && (opt->threads_x % 32 || opt->threads_x > tmax)) ||
-              (opt->threads_y && (opt->threads_y % 32 || opt->threads_y > tmax))))
-    return fail(PP_ERR_INVALID_ARG, "options: thread counts must be multiples of 32, at most %d", tmax);
+  if (opt) {
+    for (int v : {opt->threads_x, opt->threads_y, opt->threads_x_inv, opt->threads_y_inv})
+      if (v < 0 || (v && (v % 32 || v > tmax)))
+        return fail(PP_ERR_INVALID_ARG, "options: thread counts must be multiples of 32, at most %d", tmax);
+    for (int v : {opt->lines_x, opt->cols_y, opt->lines_x_inv, opt->cols_y_inv})
+      if (v < 0) return fail(PP_ERR_INVALID_ARG, "options: lines / columns per CTA must be >= 0");
+  }
   for (int v : {nx, ny})
     if (v < 2 || v > 4096 || v % 2 || !smooth23(v))
       return fail(PP_ERR_UNSUPPORTED_SIZE, "nx, ny must be even 2^a 3^b in [2, 4096] (got %d x %d)", nx, ny);
