@@ -10,8 +10,9 @@ with gcc and marshals numpy arrays through ctypes.
 
 Boundary conditions are given as a 6-letter string, one letter per face in
 the order x-, x+, y-, y+, z-, z+: ``P`` periodic (both faces of an axis),
-``N`` homogeneous Neumann, ``D`` homogeneous Dirichlet.  Grids are real
-arrays of shape (nz, ny, nx), x fastest.
+``N`` Neumann, ``D`` Dirichlet (homogeneous unless face data are given to the
+``*_g`` / ``fold_bc`` functions).  Grids are real arrays of shape (nz, ny, nx), x
+fastest.
 """
 from __future__ import annotations
 
@@ -65,6 +66,9 @@ def _load():
             lib.oracle_eigenvalue.restype = ctypes.c_double
             lib.oracle_axis_kind.argtypes = [ctypes.c_int, ctypes.c_int]
             lib.oracle_num_threads.argtypes = []
+            dpp = ctypes.POINTER(dp)
+            lib.oracle_laplacian_g.argtypes = [ctypes.c_int] * 3 + [ip] + [ctypes.c_double] * 3 + [dpp, dp, dp]
+            lib.oracle_fold_bc.argtypes = [ctypes.c_int] * 3 + [ip] + [ctypes.c_double] * 3 + [dpp, dp, dp]
             _lib = lib
     return _lib
 
@@ -120,6 +124,55 @@ def laplacian_at(u: np.ndarray, bc: str, spacing, idx: np.ndarray) -> np.ndarray
     if rc != 0:
         raise ValueError("oracle_laplacian_at failed with code %d" % rc)
     return out
+
+
+def _faces(faces, shape, bc):
+    """Face data as a ctypes double** (None entries: homogeneous faces) plus the arrays kept alive."""
+    nz, ny, nx = shape
+    fshape = [(nz, ny), (nz, ny), (nz, nx), (nz, nx), (ny, nx), (ny, nx)]
+    keep = []
+    arr = (ctypes.POINTER(ctypes.c_double) * 6)()
+    for i in range(6):
+        v = None if faces is None else faces[i]
+        if v is None:
+            arr[i] = ctypes.POINTER(ctypes.c_double)()
+            continue
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        if v.shape != fshape[i]:
+            raise ValueError("face %d data must have shape %s" % (i, fshape[i]))
+        keep.append(v)
+        arr[i] = _dp(v)
+    return arr, keep
+
+
+def laplacian_g(u: np.ndarray, bc: str, spacing, faces) -> np.ndarray:
+    """L_g u: the 7-point Laplacian whose ghosts carry face data (Dirichlet values, Neumann
+    outward normal derivatives); faces = 6 entries (x-,x+,y-,y+,z-,z+), None = homogeneous."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    nz, ny, nx = u.shape
+    arr, keep = _faces(faces, u.shape, bc)
+    out = np.empty_like(u)
+    rc = _load().oracle_laplacian_g(nx, ny, nz, _bc(bc), *map(float, spacing), arr, _dp(u), _dp(out))
+    if rc != 0:
+        raise ValueError("oracle_laplacian_g failed with code %d" % rc)
+    return out
+
+
+def fold_bc(f: np.ndarray, bc: str, spacing, faces) -> np.ndarray:
+    """f - L_g(0): the source of the homogeneous problem equivalent to L_g u = f."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    nz, ny, nx = f.shape
+    arr, keep = _faces(faces, f.shape, bc)
+    out = np.empty_like(f)
+    rc = _load().oracle_fold_bc(nx, ny, nz, _bc(bc), *map(float, spacing), arr, _dp(f), _dp(out))
+    if rc != 0:
+        raise ValueError("oracle_fold_bc failed with code %d" % rc)
+    return out
+
+
+def solve_g(f: np.ndarray, bc: str, spacing, faces) -> np.ndarray:
+    """u with L_g u = f (zero-mean u of the projected problem when no face is Dirichlet)."""
+    return solve(fold_bc(f, bc, spacing, faces), bc, spacing)
 
 
 def line_forward(kind: int, x: np.ndarray) -> np.ndarray:

@@ -307,6 +307,72 @@ int oracle_laplacian_at(int nx, int ny, int nz, const int* bc, double dx, double
   return 0;
 }
 
+/* Faces with data (the step before the path in an incompressible-flow projection; the paper's
+ * Sec. "Boundary Conditions" defines the Dirichlet ghost by linear extrapolation to the face
+ * value): Dirichlet face value g gives the ghost u_ghost = 2 g - u_inside; Neumann data q is the
+ * outward normal derivative, (u_ghost - u_inside) / h = q, so u_ghost = u_inside + h q.  With these
+ * ghosts the stencil is an affine operator L_g u = A_h u + L_g(0).
+ * g[face]: NULL (homogeneous face) or the face's values, faces x-,x+,y-,y+,z-,z+; x faces are
+ * [nz][ny], y faces [nz][nx], z faces [ny][nx].  A periodic face must have no data. */
+static double face_value(const double* const* g, int face, int i, int j, int k, int nx, int ny) {
+  const double* v = g ? g[face] : NULL;
+  if (!v) return 0.0;
+  if (face < 2) return v[(size_t)k * ny + j];
+  if (face < 4) return v[(size_t)k * nx + i];
+  return v[(size_t)j * nx + i];
+}
+
+static inline double ghost_g(int bc, double inside, double data, double h) {
+  return (bc == OR_BC_N) ? inside + h * data : 2.0 * data - inside;
+}
+
+/* L_g u: the 7-point Laplacian with the data ghosts above. */
+int oracle_laplacian_g(int nx, int ny, int nz, const int* bc, double dx, double dy, double dz,
+                       const double* const* g, const double* u, double* out) {
+  if (nx < 1 || ny < 1 || nz < 1) return -1;
+  if (check_bc(bc)) return -3;
+  for (int f = 0; f < 6; f++)
+    if (g && g[f] && bc[f] == OR_BC_P) return -4;
+  double ix2 = 1.0 / (dx * dx), iy2 = 1.0 / (dy * dy), iz2 = 1.0 / (dz * dz);
+  size_t sy = (size_t)nx, sz = (size_t)nx * ny;
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int k = 0; k < nz; k++)
+    for (int j = 0; j < ny; j++)
+      for (int i = 0; i < nx; i++) {
+        size_t p = (size_t)k * sz + (size_t)j * sy + i;
+        double c = u[p], xm, xp, ym, yp, zm, zp;
+        if (i > 0) xm = u[p - 1];
+        else xm = (bc[0] == OR_BC_P) ? u[p + nx - 1] : ghost_g(bc[0], c, face_value(g, 0, i, j, k, nx, ny), dx);
+        if (i < nx - 1) xp = u[p + 1];
+        else xp = (bc[1] == OR_BC_P) ? u[p - (nx - 1)] : ghost_g(bc[1], c, face_value(g, 1, i, j, k, nx, ny), dx);
+        if (j > 0) ym = u[p - sy];
+        else ym = (bc[2] == OR_BC_P) ? u[p + (ny - 1) * sy] : ghost_g(bc[2], c, face_value(g, 2, i, j, k, nx, ny), dy);
+        if (j < ny - 1) yp = u[p + sy];
+        else yp = (bc[3] == OR_BC_P) ? u[p - (ny - 1) * sy] : ghost_g(bc[3], c, face_value(g, 3, i, j, k, nx, ny), dy);
+        if (k > 0) zm = u[p - sz];
+        else zm = (bc[4] == OR_BC_P) ? u[p + (nz - 1) * sz] : ghost_g(bc[4], c, face_value(g, 4, i, j, k, nx, ny), dz);
+        if (k < nz - 1) zp = u[p + sz];
+        else zp = (bc[5] == OR_BC_P) ? u[p - (nz - 1) * sz] : ghost_g(bc[5], c, face_value(g, 5, i, j, k, nx, ny), dz);
+        out[p] = (xm - 2.0 * c + xp) * ix2 + (ym - 2.0 * c + yp) * iy2 + (zm - 2.0 * c + zp) * iz2;
+      }
+  return 0;
+}
+
+/* The problem L_g u = f is A_h u = f - L_g(0): out = f - L_g(0) (out may alias f). */
+int oracle_fold_bc(int nx, int ny, int nz, const int* bc, double dx, double dy, double dz,
+                   const double* const* g, const double* f, double* out) {
+  size_t n = (size_t)nx * ny * nz;
+  double* zero = (double*)calloc(n, sizeof(double));
+  double* l0 = (double*)malloc(n * sizeof(double));
+  if (!zero || !l0) { free(zero); free(l0); return -2; }
+  int rc = oracle_laplacian_g(nx, ny, nz, bc, dx, dy, dz, g, zero, l0);
+  if (rc == 0)
+    for (size_t p = 0; p < n; p++) out[p] = f[p] - l0[p];
+  free(zero);
+  free(l0);
+  return rc;
+}
+
 int oracle_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();
