@@ -128,6 +128,26 @@ pp_status pp_solve_refined(pp_plan* plan, const void* f_dev, void* u_dev, pp_str
  * them.  Asynchronous on stream like pp_solve. */
 pp_status pp_solve_refined_noalloc(pp_plan* plan, const void* f_dev, void* u_dev, pp_stream_t stream);
 
+/* Faces with data (non-homogeneous boundary conditions): folds face values into a source so that
+ * pp_solve then solves the problem with those faces.  The ghost rules are the paper's (Sec.
+ * "Boundary Conditions": the Dirichlet ghost extrapolates linearly to the face value):
+ *   Dirichlet face value g:                u_ghost = 2 g - u_inside,
+ *   Neumann data q (outward normal derivative): u_ghost = u_inside + h q,
+ * so the stencil becomes L_g u = A u + L_g(0), and L_g u = f is A u = f - L_g(0).  This call
+ * writes f_out = f_in - L_g(0): on the cells next to a face with data it subtracts 2 g / h^2
+ * (Dirichlet) or q / h (Neumann), h the spacing normal to the face (edge and corner cells get
+ * the terms of all their faces).
+ *   g      : 6 pointers, faces x-,x+,y-,y+,z-,z+; NULL = homogeneous face (no term).  Device
+ *            arrays of the plan's I/O type: x faces [nz][ny], y faces [nz][nx], z faces [ny][nx]
+ *            (the face's cells in the grid's order).  A periodic face must be NULL.
+ *   f_in   : device grid (nx*ny*nz, I/O type); f_out: device grid, may alias f_in (then only the
+ *            face cells are rewritten; otherwise f_in is copied first).
+ * With no Dirichlet face the solve removes the mean of the folded source (the compatibility
+ * condition of the Neumann data), as for homogeneous faces.  FP64 arithmetic.  Asynchronous
+ * on stream.  Errors: PP_ERR_INVALID_ARG (NULL plan / grid, data on a periodic face),
+ * PP_ERR_CUDA (launch). */
+pp_status pp_fold_bc(pp_plan* plan, const void* f_in, void* f_out, const void* const g[6], pp_stream_t stream);
+
 /* Solve n independent problems, plans[i] applied to (f[i] -> u[i]) -- grids of any sizes,
  * boundary sets and dtypes -- as ONE CUDA-graph launch on `stream`.  The first call with a
  * given (plans, f, u) list captures the n five-kernel pipelines into a graph and instantiates

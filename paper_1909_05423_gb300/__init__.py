@@ -7,8 +7,9 @@ sm_103a kernels behind the C ABI of ``include/pittpack_gb.h``.  This module only
 torch tensors (device memory, streams) into that ABI.
 
 Boundary conditions are a 6-letter string over faces x-, x+, y-, y+, z-, z+ with ``P``
-(periodic, both faces of an axis), ``N`` (Neumann) or ``D`` (homogeneous Dirichlet).
-Grids are tensors of shape (nz, ny, nx).
+(periodic, both faces of an axis), ``N`` (Neumann) or ``D`` (Dirichlet); faces are
+homogeneous unless face data are folded in (``Plan.fold_bc``).  Grids are tensors of shape
+(nz, ny, nx).
 """
 from __future__ import annotations
 
@@ -109,6 +110,39 @@ class Plan:
                                              ctypes.c_void_p(out_host.data_ptr()), _stream_handle(stream)))
         return out_host
 
+    def face_shapes(self):
+        """Shapes of the face-data arrays, faces x-, x+, y-, y+, z-, z+."""
+        nz, ny, nx = self.shape
+        return [(nz, ny), (nz, ny), (nz, nx), (nz, nx), (ny, nx), (ny, nx)]
+
+    def fold_bc(self, f, faces, out=None, stream=None):
+        """Source of the homogeneous problem equivalent to faces with data: faces = 6 entries
+        (x-, x+, y-, y+, z-, z+), None for a homogeneous face, else a CUDA tensor of the face's
+        shape (``face_shapes``) holding the Dirichlet face values or the Neumann outward normal
+        derivatives.  out may be f (in place)."""
+        import torch
+        self._check_tensor(f, "f")
+        if out is None:
+            out = torch.empty_like(f)
+        self._check_tensor(out, "out")
+        if len(faces) != 6:
+            raise ValueError("faces must have 6 entries (x-, x+, y-, y+, z-, z+)")
+        ptrs = (ctypes.c_void_p * 6)()
+        for i, (g, shp) in enumerate(zip(faces, self.face_shapes())):
+            if g is None:
+                continue
+            if (not isinstance(g, torch.Tensor) or not g.is_cuda or tuple(g.shape) != shp or g.dtype != self.io_dtype
+                    or not g.is_contiguous()):
+                raise ValueError("face %d data must be a contiguous CUDA %s tensor of shape %s" % (i, self.io_dtype, shp))
+            ptrs[i] = g.data_ptr()
+        _lib.check(_lib.load().pp_fold_bc(self._h, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                          ptrs, _stream_handle(stream)))
+        return out
+
+    def solve_bc(self, f, faces, out=None, stream=None):
+        """Solve with faces with data: fold them into a copy of f, then solve."""
+        return self.solve(self.fold_bc(f, faces, stream=stream), out=out, stream=stream)
+
     def status(self):
         _lib.check(_lib.load().pp_plan_status(self._h))
 
@@ -127,10 +161,13 @@ class Plan:
             pass
 
 
-def solve(f, bc: str, spacing=(1.0, 1.0, 1.0), dtype: str = "f64", refined: bool = False):
-    """One-shot solve of Laplacian_h(u) = f on a CUDA tensor f of shape (nz, ny, nx)."""
+def solve(f, bc: str, spacing=(1.0, 1.0, 1.0), dtype: str = "f64", refined: bool = False, faces=None):
+    """One-shot solve of Laplacian_h(u) = f on a CUDA tensor f of shape (nz, ny, nx); faces:
+    optional face data (see Plan.fold_bc)."""
     plan = Plan(tuple(f.shape), bc, spacing, dtype)
     try:
+        if faces is not None:
+            f = plan.fold_bc(f, faces)
         return plan.solve_refined(f) if refined else plan.solve(f)
     finally:
         import torch

@@ -19,9 +19,9 @@ BC_CODE = {"P": 0, "N": 1, "D": 2}
 DTYPES = {"f64": 0, "mixed_f64io": 1, "mixed_f32io": 2}
 
 # every entry point declared in include/pittpack_gb.h
-EXPORTS = ["pp_plan_create", "pp_solve", "pp_solve_refined", "pp_solve_refined_noalloc", "pp_solve_batched", "pp_solve_adjoint",
-           "pp_solve_host", "pp_run_stage", "pp_plan_destroy", "pp_plan_status", "pp_plan_device_bytes", "pp_last_error_string",
-           "pp_version"]
+EXPORTS = ["pp_plan_create", "pp_solve", "pp_solve_refined", "pp_solve_refined_noalloc", "pp_fold_bc", "pp_solve_batched",
+           "pp_solve_adjoint", "pp_solve_host", "pp_run_stage", "pp_plan_destroy", "pp_plan_status", "pp_plan_device_bytes",
+           "pp_last_error_string", "pp_version"]
 
 
 class PPError(RuntimeError):
@@ -65,6 +65,8 @@ def load():
         lib.pp_run_stage.restype = ctypes.c_int
         lib.pp_solve_batched.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int, vp]
         lib.pp_solve_batched.restype = ctypes.c_int
+        lib.pp_fold_bc.argtypes = [vp, vp, vp, ctypes.POINTER(vp), vp]
+        lib.pp_fold_bc.restype = ctypes.c_int
         lib.pp_plan_destroy.argtypes = [vp]
         lib.pp_plan_destroy.restype = ctypes.c_int
         lib.pp_plan_status.argtypes = [vp]

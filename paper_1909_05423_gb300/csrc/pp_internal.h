@@ -140,6 +140,9 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
 cudaError_t launch_zsolve(const pp_plan* p, void* data, int transpose, cudaStream_t st);
 cudaError_t launch_residual(const pp_plan* p, const void* f, const void* u, void* r, cudaStream_t st);
 cudaError_t launch_add(const pp_plan* p, void* u, const void* d, const void* shift, cudaStream_t st);
+// f -= coef * g on the cells next to face `face` (0..5 = x-,x+,y-,y+,z-,z+), in place
+cudaError_t launch_fold_face(void* f, const void* g, int nx, int ny, int nz, int face, double coef, bool f32,
+                             cudaStream_t st);
 // n pseudo-random values in [-1, 1) (FP32 or FP64), timing input of the autotuner
 cudaError_t launch_fill(void* x, long long n, bool f32, cudaStream_t st);
 // mean of an FP64 grid: nparts block sums into `partials` (nparts float2), result (hi,lo) into `mean`

@@ -122,6 +122,39 @@ cudaError_t launch_mean(const pp_plan* p, const void* u, void* partials, int npa
   return cudaGetLastError();
 }
 
+// Faces with data: f -= coef * g on the cells next to one face (coef = 2/h^2 Dirichlet, 1/h
+// Neumann).  Face arrays are [a0][a1]: x faces (k, j), y faces (k, i), z faces (j, i).  One launch
+// per face, in sequence on the stream, so edge and corner cells take every face's term.
+__global__ void k_fold_face(void* f, const void* g, int nx, int ny, int nz, int face, double coef, int f32) {
+  const int axis = face >> 1, hi = face & 1;
+  const long long n1 = (axis == 0) ? ny : nx;
+  const long long n0 = (axis == 2) ? ny : nz;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n0 * n1) return;
+  const int a0 = (int)(t / n1), a1 = (int)(t - (t / n1) * n1);
+  int i, j, k;
+  if (axis == 0) { k = a0; j = a1; i = hi ? nx - 1 : 0; }
+  else if (axis == 1) { k = a0; i = a1; j = hi ? ny - 1 : 0; }
+  else { j = a0; i = a1; k = hi ? nz - 1 : 0; }
+  const long long p = ((long long)k * ny + j) * nx + i;
+  if (f32) {
+    float* fp = reinterpret_cast<float*>(f);
+    const double v = __fma_rn(-coef, (double)reinterpret_cast<const float*>(g)[t], (double)fp[p]);
+    fp[p] = __double2float_rn(v);
+  } else {
+    double* fp = reinterpret_cast<double*>(f);
+    fp[p] = __fma_rn(-coef, reinterpret_cast<const double*>(g)[t], fp[p]);
+  }
+}
+
+cudaError_t launch_fold_face(void* f, const void* g, int nx, int ny, int nz, int face, double coef, bool f32,
+                             cudaStream_t st) {
+  const int axis = face >> 1;
+  const long long n = (long long)(axis == 2 ? ny : nz) * (axis == 0 ? ny : nx);
+  k_fold_face<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(f, g, nx, ny, nz, face, coef, f32 ? 1 : 0);
+  return cudaGetLastError();
+}
+
 // Timing input of the autotuner: values in [-1, 1) from an integer hash of the index (no
 // statistical quality needed, only normal non-constant data).
 __global__ void k_fill(void* x, long long n, int f32) {

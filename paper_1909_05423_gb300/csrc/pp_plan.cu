@@ -839,6 +839,30 @@ pp_status pp_solve_adjoint(pp_plan* p, const void* g, void* gf, pp_stream_t stre
   return run_pipeline(p, g, gf, 1, (cudaStream_t)stream);
 }
 
+pp_status pp_fold_bc(pp_plan* p, const void* f_in, void* f_out, const void* const g[6], pp_stream_t stream) {
+  if (!p || !f_in || !f_out || !g) return fail(PP_ERR_INVALID_ARG, "NULL plan or pointer");
+  for (int face = 0; face < 6; face++)
+    if (g[face] && p->bc[face] == PP_BC_PERIODIC)
+      return fail(PP_ERR_INVALID_ARG, "face %d is periodic and takes no data", face);
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool f32 = (p->dtype == PP_MIXED_F32IO);
+  if (f_in != f_out) {
+    const size_t bytes = (size_t)p->nx * p->ny * p->nz * (f32 ? 4 : 8);
+    cudaError_t e = cudaMemcpyAsync(f_out, f_in, bytes, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return fail(PP_ERR_CUDA, "copy of the source: %s", cudaGetErrorString(e));
+  }
+  const double h[3] = {p->dx, p->dy, p->dz};
+  for (int face = 0; face < 6; face++) {
+    if (!g[face]) continue;
+    const double hn = h[face >> 1];
+    // L_g(0) next to the face: ghost / h^2 with ghost 2 g (Dirichlet) or h q (Neumann)
+    const double coef = (p->bc[face] == PP_BC_DIRICHLET) ? 2.0 * (1.0 / (hn * hn)) : hn * (1.0 / (hn * hn));
+    cudaError_t e = launch_fold_face(f_out, g[face], p->nx, p->ny, p->nz, face, coef, f32, st);
+    if (e != cudaSuccess) return fail(PP_ERR_CUDA, "face %d launch: %s", face, cudaGetErrorString(e));
+  }
+  return PP_OK;
+}
+
 pp_status pp_solve_refined(pp_plan* p, const void* f, void* u, pp_stream_t stream) {
   if (!p || !f || !u) return fail(PP_ERR_INVALID_ARG, "NULL plan or pointer");
   if (p->dtype != PP_MIXED_F64IO) return fail(PP_ERR_INVALID_ARG, "refinement needs a PP_MIXED_F64IO plan");

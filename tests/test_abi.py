@@ -79,6 +79,13 @@ def test_null_arguments(lib):
     assert lib.pp_solve_batched(None, None, None, -1, None) == 1
 
 
+def test_fold_bc_rejects_null_arguments(lib):
+    vp = ctypes.c_void_p
+    faces = (vp * 6)()
+    assert lib.pp_fold_bc(None, None, None, faces, None) == 1  # PP_ERR_INVALID_ARG, no device work
+    assert lib.pp_fold_bc(None, vp(16), vp(16), None, None) == 1
+
+
 def test_fault_injection_alloc_fails_cleanly(lib, monkeypatch):
     """An injected allocation failure is reported as PP_ERR_OUT_OF_MEMORY with a message and no
     plan; the failure is made on the host before any device work (runs without a GPU)."""
