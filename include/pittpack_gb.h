@@ -22,12 +22,12 @@
  *    homogeneous: periodic (must be given on both faces of an axis), Neumann
  *    (ghost u[-1] = u[0]) or Dirichlet with zero face value by linear
  *    extrapolation (ghost u[-1] = -u[0], Sec. "Dirichlet-type Boundary
- *    Condition").  Non-zero face values are folded into f by the caller.
+ *    Condition").  Non-zero face values are folded into f by pp_fold_bc.
  *  - With no Dirichlet face the operator is singular (Sec. "Well-posedness");
  *    the library then returns the zero-mean u with A u = f - mean(f).
- *  - Sizes: nx and ny must be even and of the form 2^a 3^b (a >= 1),
- *    2 <= nx, ny <= 4096; nz >= 2 (periodic z: nz >= 3).  Anything else
- *    returns PP_ERR_UNSUPPORTED_SIZE.
+ *  - Sizes: nx and ny must be even and of the form 2^a 3^b 5^c 7^d (a >= 1;
+ *    FFT radices 2, 3, 4, 5, 7, 8), 2 <= nx, ny <= 4096; nz >= 2 (periodic z:
+ *    nz >= 3).  Anything else returns PP_ERR_UNSUPPORTED_SIZE.
  *  - All solve calls are asynchronous on the given CUDA stream (NULL = legacy
  *    default stream).  The returned status reports argument validation and
  *    launch errors; device-side errors are reported by pp_plan_status() after

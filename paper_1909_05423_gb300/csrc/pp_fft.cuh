@@ -1,4 +1,4 @@
-// pp_fft.cuh -- shared-memory mixed-radix (2,3,4,8) Stockham FFT for a batch of lines.
+// pp_fft.cuh -- shared-memory mixed-radix (2,3,4,5,7,8) Stockham FFT for a batch of lines.
 //
 // The complex DFT Y_k = sum_n z_n exp(-2 pi i n k / M) (Sec. "Periodic Boundary Condition")
 // of every line of a CTA is computed in place in shared memory by the Stockham
@@ -42,14 +42,17 @@ struct FastDiv {
   }
 };
 
-// butterflies per thread per stage
+// butterflies per thread per stage (NB * radix >= 8 for every radix)
 template <int RAD> struct NBut;
 template <> struct NBut<2> { static constexpr int v = 4; };
 template <> struct NBut<3> { static constexpr int v = 3; };
 template <> struct NBut<4> { static constexpr int v = 2; };
+template <> struct NBut<5> { static constexpr int v = 2; };
+template <> struct NBut<7> { static constexpr int v = 2; };
 template <> struct NBut<8> { static constexpr int v = 1; };
-// complex values a thread holds per stage: 8 for radix 2/4/8, 9 for radix 3.  A launch is valid
-// only if lines_per_cta * M <= kCapPerThread * threads (checked on the host before every launch).
+// complex values a thread holds per stage: 8 for radix 2/4/8, 9 / 10 / 14 for radix 3 / 5 / 7.  A
+// launch is valid only if lines_per_cta * M <= kCapPerThread * threads (checked on the host before
+// every launch): then no stage has more butterflies than NB * threads.
 constexpr int kCapPerThread = 8;
 constexpr int kCapPerThread3 = 8;
 
@@ -108,10 +111,59 @@ template <class R, bool INV> __device__ __forceinline__ void dft8(cx<R>* a) {
   }
 }
 
+// A constant of the arithmetic type from its FP32 split hi + lo (FP32 keeps hi, the nearest float).
+template <class R> __device__ __forceinline__ R kconst(float hi, float lo);
+template <> __device__ __forceinline__ float kconst<float>(float hi, float) { return hi; }
+template <> __device__ __forceinline__ df kconst<df>(float hi, float lo) { return df{hi, lo}; }
+
+// 5-point DFT.  With t1 = a1 + a4, t2 = a2 + a3, t3 = a1 - a4, t4 = a2 - a3 and c_k, s_k =
+// cos, sin(2 pi k / 5):  Y_1, Y_4 = a0 + c1 t1 + c2 t2 -+ i (s1 t3 + s2 t4),
+// Y_2, Y_3 = a0 + c2 t1 + c1 t2 -+ i (s2 t3 - s1 t4);  the inverse takes the other sign of i.
+template <class R, bool INV> __device__ __forceinline__ void dft5(cx<R>* a) {
+  const R c1 = kconst<R>(0x1.3c6ef4p-2f, -0x1.1a02d6p-27f), c2 = kconst<R>(-0x1.9e377ap-1f, 0x1.1a02d6p-27f);
+  const R s1 = kconst<R>(0x1.e6f0e2p-1f, -0x1.977560p-26f), s2 = kconst<R>(0x1.2cf230p-1f, 0x1.1d5698p-27f);
+  const cx<R> t1 = cadd(a[1], a[4]), t2 = cadd(a[2], a[3]), t3 = csub(a[1], a[4]), t4 = csub(a[2], a[3]);
+  const cx<R> A1 = cadd(a[0], cadd(cscale(t1, c1), cscale(t2, c2)));
+  const cx<R> A2 = cadd(a[0], cadd(cscale(t1, c2), cscale(t2, c1)));
+  const cx<R> B1 = cmul_mi<R, INV>(cadd(cscale(t3, s1), cscale(t4, s2)));
+  const cx<R> B2 = cmul_mi<R, INV>(csub(cscale(t3, s2), cscale(t4, s1)));
+  a[0] = cadd(a[0], cadd(t1, t2));
+  a[1] = cadd(A1, B1);
+  a[4] = csub(A1, B1);
+  a[2] = cadd(A2, B2);
+  a[3] = csub(A2, B2);
+}
+
+// 7-point DFT.  With t_m = a_m + a_{7-m}, u_m = a_m - a_{7-m} (m = 1..3) and c_j, s_j =
+// cos, sin(2 pi j / 7):  Y_k, Y_{7-k} = a0 + sum_m cos(2 pi k m/7) t_m -+ i sum_m sin(2 pi k m/7) u_m,
+// k = 1..3 (cos(2 pi k m/7) = c_{km mod 7}, c_{7-j} = c_j, s_{7-j} = -s_j).
+template <class R, bool INV> __device__ __forceinline__ void dft7(cx<R>* a) {
+  const R c1 = kconst<R>(0x1.3f3a0ep-1f, 0x1.45f6e8p-28f), c2 = kconst<R>(-0x1.c7b90ep-3f, -0x1.8122c0p-30f);
+  const R c3 = kconst<R>(-0x1.cd4bcap-1f, -0x1.396b8ep-26f), s1 = kconst<R>(0x1.904c38p-1f, -0x1.5f4436p-26f);
+  const R s2 = kconst<R>(0x1.f329c0p-1f, 0x1.563a5ap-27f), s3 = kconst<R>(0x1.bc4c04p-2f, 0x1.ae3578p-27f);
+  const cx<R> t1 = cadd(a[1], a[6]), t2 = cadd(a[2], a[5]), t3 = cadd(a[3], a[4]);
+  const cx<R> u1 = csub(a[1], a[6]), u2 = csub(a[2], a[5]), u3 = csub(a[3], a[4]);
+  const cx<R> A1 = cadd(a[0], cadd(cadd(cscale(t1, c1), cscale(t2, c2)), cscale(t3, c3)));
+  const cx<R> A2 = cadd(a[0], cadd(cadd(cscale(t1, c2), cscale(t2, c3)), cscale(t3, c1)));
+  const cx<R> A3 = cadd(a[0], cadd(cadd(cscale(t1, c3), cscale(t2, c1)), cscale(t3, c2)));
+  const cx<R> B1 = cmul_mi<R, INV>(cadd(cadd(cscale(u1, s1), cscale(u2, s2)), cscale(u3, s3)));
+  const cx<R> B2 = cmul_mi<R, INV>(csub(csub(cscale(u1, s2), cscale(u2, s3)), cscale(u3, s1)));
+  const cx<R> B3 = cmul_mi<R, INV>(cadd(csub(cscale(u1, s3), cscale(u2, s1)), cscale(u3, s2)));
+  a[0] = cadd(a[0], cadd(cadd(t1, t2), t3));
+  a[1] = cadd(A1, B1);
+  a[6] = csub(A1, B1);
+  a[2] = cadd(A2, B2);
+  a[5] = csub(A2, B2);
+  a[3] = cadd(A3, B3);
+  a[4] = csub(A3, B3);
+}
+
 template <class R, int RAD, bool INV> __device__ __forceinline__ void dft_r(cx<R>* a) {
-  if (RAD == 2) dft2<R, INV>(a);
-  else if (RAD == 3) dft3<R, INV>(a);
-  else if (RAD == 4) dft4<R, INV>(a);
+  if constexpr (RAD == 2) dft2<R, INV>(a);
+  else if constexpr (RAD == 3) dft3<R, INV>(a);
+  else if constexpr (RAD == 4) dft4<R, INV>(a);
+  else if constexpr (RAD == 5) dft5<R, INV>(a);
+  else if constexpr (RAD == 7) dft7<R, INV>(a);
   else dft8<R, INV>(a);
 }
 
@@ -181,6 +233,8 @@ __device__ __forceinline__ void fft_lines(cx<R>* buf, int nlines, int ldm, const
     if (r == 8) fft_stage<R, 8, INV>(buf, nlines, ldm, s, fp.nbl[st], fp.s[st], tw);
     else if (r == 4) fft_stage<R, 4, INV>(buf, nlines, ldm, s, fp.nbl[st], fp.s[st], tw);
     else if (r == 3) fft_stage<R, 3, INV>(buf, nlines, ldm, s, fp.nbl[st], fp.s[st], tw);
+    else if (r == 5) fft_stage<R, 5, INV>(buf, nlines, ldm, s, fp.nbl[st], fp.s[st], tw);
+    else if (r == 7) fft_stage<R, 7, INV>(buf, nlines, ldm, s, fp.nbl[st], fp.s[st], tw);
     else fft_stage<R, 2, INV>(buf, nlines, ldm, s, fp.nbl[st], fp.s[st], tw);
     s *= r;
   }

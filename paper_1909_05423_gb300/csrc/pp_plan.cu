@@ -63,10 +63,11 @@ static bool inject(const char* point) {
 }
 
 // ------------------------------------------------------------------ helpers
-static bool smooth23(int n) {
+// n has no prime factor above 7 (the FFT radices are 2, 3, 4, 5, 7, 8)
+static bool smooth2357(int n) {
   if (n < 1) return false;
-  while (n % 2 == 0) n /= 2;
-  while (n % 3 == 0) n /= 3;
+  for (int p : {2, 3, 5, 7})
+    while (n % p == 0) n /= p;
   return n == 1;
 }
 
@@ -79,6 +80,8 @@ static FftPlan make_fft(int M) {
   while (m % 4 == 0 && f.nst < kMaxStages) { f.rad[f.nst++] = 4; m /= 4; }
   while (m % 2 == 0 && f.nst < kMaxStages) { f.rad[f.nst++] = 2; m /= 2; }
   while (m % 3 == 0 && f.nst < kMaxStages) { f.rad[f.nst++] = 3; m /= 3; }
+  while (m % 5 == 0 && f.nst < kMaxStages) { f.rad[f.nst++] = 5; m /= 5; }
+  while (m % 7 == 0 && f.nst < kMaxStages) { f.rad[f.nst++] = 7; m /= 7; }
   int s = 1;
   for (int i = 0; i < f.nst; i++) {
     f.nbl[i] = FastDiv::make((unsigned)(M / f.rad[i]));
@@ -764,8 +767,8 @@ pp_status pp_plan_create(pp_plan** out, int nx, int ny, int nz, const pp_bc bc[6
       if (v < 0) return fail(PP_ERR_INVALID_ARG, "options: lines / columns per CTA must be >= 0");
   }
   for (int v : {nx, ny})
-    if (v < 2 || v > 4096 || v % 2 || !smooth23(v))
-      return fail(PP_ERR_UNSUPPORTED_SIZE, "nx, ny must be even 2^a 3^b in [2, 4096] (got %d x %d)", nx, ny);
+    if (v < 2 || v > 4096 || v % 2 || !smooth2357(v))
+      return fail(PP_ERR_UNSUPPORTED_SIZE, "nx, ny must be even 2^a 3^b 5^c 7^d in [2, 4096] (got %d x %d)", nx, ny);
   bool zper = (bc[4] == PP_BC_PERIODIC);
   if (nz < (zper ? 3 : 2) || nz > (1 << 20))
     return fail(PP_ERR_UNSUPPORTED_SIZE, "nz = %d out of range (>= 2, periodic z >= 3)", nz);

@@ -46,7 +46,7 @@ def _create(lib, nx, ny, nz, bc, dx=1.0, dtype=0):
 
 
 @pytest.mark.parametrize("nx,ny,nz,bc,code", [
-    (10, 8, 8, "PPPPDD", 2),     # 10 is not 2^a 3^b
+    (22, 8, 8, "PPPPDD", 2),     # 22 has the prime factor 11 (radices 2, 3, 5, 7 only)
     (9, 8, 8, "PPPPDD", 2),      # odd
     (8, 8, 1, "PPPPDD", 2),      # nz < 2
     (8, 8, 2, "NNNNPP", 2),      # periodic z needs nz >= 3
