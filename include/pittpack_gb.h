@@ -166,10 +166,14 @@ pp_status pp_solve_batched(pp_plan* const* plans, const void* const* f, void* co
  * Same argument rules as pp_solve. */
 pp_status pp_solve_adjoint(pp_plan* plan, const void* g_dev, void* gf_dev, pp_stream_t stream);
 
-/* pp_solve on HOST buffers: copies f to the device, solves, copies u back, all on
- * stream, and synchronises the stream before returning.  Device staging buffers are
- * allocated by the first call on a plan.  f_host, u_host: nx*ny*nz elements of the
- * plan's I/O type (pinned memory gives full copy bandwidth). */
+/* pp_solve on HOST buffers: copies f to the device, solves, copies u back, and synchronises
+ * stream before returning.  The copies run in up to 8 plane chunks on two copy streams owned
+ * by the plan: the host->device copy of a chunk overlaps the x/y forward transforms of the
+ * chunks before it, the device->host copy of a chunk the inverse transforms of the chunks
+ * after it (the z solve needs every plane, so it sits between the two halves).  Device staging
+ * buffers and the streams are created by the first call on a plan.  f_host, u_host:
+ * nx*ny*nz elements of the plan's I/O type (pinned memory gives full copy bandwidth and
+ * lets the copies overlap).  Calls on one plan must not overlap. */
 pp_status pp_solve_host(pp_plan* plan, const void* f_host, void* u_host, pp_stream_t stream);
 
 /* Run one stage of the pp_solve pipeline on its own (for per-kernel timing and profiling):

@@ -58,6 +58,7 @@ struct LineArgs {
   FastDiv fd_gpc;     // y: groups of vector-width adjacent lines per CTA
 };
 constexpr int kMaxLpc = 512;  // lines per CTA (bounded so the per-line bases fit in shared memory)
+constexpr int kHostChunks = 8;  // plane chunks of a host-buffer solve (copies overlap transforms)
 
 // Complex FFT lengths with kernels compiled for the length: powers of two 64..1024.  Their stage
 // twiddles are stored per stage in butterfly order (fft_lines_ct); other lengths keep w_M^j, j < M.
@@ -130,13 +131,16 @@ struct pp_plan {
   void* d_mean;        // kMeanParts partial sums + 1 mean (float2 each), singular refinement
   void* d_host_f;      // device staging for host-buffer solves
   void* d_host_u;
+  cudaStream_t host_cs[2];  // copy streams of host-buffer solves (created on first use)
+  cudaEvent_t host_ev[2 * pp::kHostChunks + 3];  // per-chunk copy / compute events, start, two joins
   int* d_status;
 };
 
 namespace pp {
 // launchers (return cudaError_t of the launch)
+// line stage over planes z0 .. z0+nzc-1 (nzc < 0: all); in / out point at plane 0
 cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_out, const void* in, void* out,
-                         cudaStream_t st);
+                         cudaStream_t st, int z0 = 0, int nzc = -1);
 cudaError_t launch_zsolve(const pp_plan* p, void* data, int transpose, cudaStream_t st);
 cudaError_t launch_residual(const pp_plan* p, const void* f, const void* u, void* r, cudaStream_t st);
 cudaError_t launch_add(const pp_plan* p, void* u, const void* d, const void* shift, cudaStream_t st);

@@ -360,6 +360,10 @@ static void free_plan(pp_plan* p) {
                   p->d_qtab, p->d_resid, p->d_mean, p->d_host_f, p->d_host_u, p->d_status};
   for (void* q : ptrs)
     if (q) cudaFree(q);
+  for (cudaStream_t s : p->host_cs)
+    if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : p->host_ev)
+    if (e) cudaEventDestroy(e);
   delete p;
 }
 
@@ -461,19 +465,22 @@ static void finish_args(LineArgs& a) {
 
 namespace pp {
 // axis 0 = x, 1 = y; dir 0 = forward, 1 = inverse.  io_in / io_out: ST_* codes.
+// bytes per real of a storage code
+static size_t st_bytes(const pp_plan* p, int code) { return code == ST_F64 ? 8 : (code == ST_F32 ? 4 : p->elem); }
+
 cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_out, const void* in, void* out,
-                         cudaStream_t st) {
+                         cudaStream_t st, int z0, int nzc) {
   LineArgs a;
   memset(&a, 0, sizeof a);
-  a.in = in;
-  a.out = out;
+  if (nzc < 0) { z0 = 0; nzc = p->nz; }
+  if (z0 < 0 || nzc < 1 || z0 + nzc > p->nz) return cudaErrorInvalidValue;
   const bool dfm = (p->dtype == PP_F64);
   const long long nxy = (long long)p->nx * p->ny;
   if (axis == 0) {
     bool per = (p->kx == AX_P);
     a.N = p->nx;
     a.kind = dir == 0 ? fwd_kind(p->kx, false) : inv_kind(p->kx, false);
-    a.nlines = p->ny * p->nz;
+    a.nlines = p->ny * nzc;
     a.lines_per_plane = p->ny;
     a.parts = 1;
     a.lpc = p->lpc_x[dir];
@@ -490,6 +497,11 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
       a.in_plane = sp_plane; a.in_line = (int)sp_row; a.in_pos = per ? 2 : 1;
       a.out_plane = grid_plane; a.out_line = grid_row; a.out_pos = 1;
     }
+    // planes z0 .. z0+nzc-1
+    in = static_cast<const char*>(in) + (size_t)z0 * a.in_plane * st_bytes(p, io_in);
+    out = static_cast<char*>(out) + (size_t)z0 * a.out_plane * st_bytes(p, io_out);
+    a.in = in;
+    a.out = out;
     if ((long long)a.lpc * a.fp.M > (long long)kCapPerThread * p->threads_x[dir]) return cudaErrorInvalidConfiguration;
     a.ntiles = (a.nlines + a.lpc - 1) / a.lpc;
     a.vec_ok = (((uintptr_t)in | (uintptr_t)out) % 32 == 0) ? 1 : 0;
@@ -505,7 +517,7 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
   int ncols = cplx_cols ? p->nx / 2 + 1 : p->nx;
   a.parts = parts;
   a.lines_per_plane = ncols * parts;
-  a.nlines = a.lines_per_plane * p->nz;
+  a.nlines = a.lines_per_plane * nzc;
   a.lpc = p->lpc_y[dir];
   a.ldm = p->ldm_y;
   a.fp = p->fy;
@@ -524,11 +536,16 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
     a.in_plane = s_plane; a.in_line = (int)s_col; a.in_pos = (int)s_pos;
     a.out_plane = xs_plane; a.out_line = xs_col; a.out_pos = xs_pos;
   }
+  // planes z0 .. z0+nzc-1
+  in = static_cast<const char*>(in) + (size_t)z0 * a.in_plane * st_bytes(p, io_in);
+  out = static_cast<char*>(out) + (size_t)z0 * a.out_plane * st_bytes(p, io_out);
+  a.in = in;
+  a.out = out;
   if ((long long)a.lpc * a.fp.M > (long long)kCapPerThread * p->threads_y[dir]) return cudaErrorInvalidConfiguration;
   a.tx = a.lpc / parts;
   a.ncols = ncols;
   a.nblk = (ncols + a.tx - 1) / a.tx;
-  a.ntiles = a.nblk * p->nz;
+  a.ntiles = a.nblk * nzc;
   {
     // 16-byte vectors of V adjacent real lines: the tile row must be contiguous (line L at real
     // offset L) and every vector start aligned (checked through all strides and both pointers)
@@ -567,16 +584,19 @@ cudaError_t launch_zsolve(const pp_plan* p, void* data, int transpose, cudaStrea
 }
 }  // namespace pp
 
-static pp_status run_stage(pp_plan* p, int stage, const void* f, void* u, int transpose, cudaStream_t st) {
+// One stage of the pipeline; the line stages may be restricted to planes z0 .. z0+nzc-1 (nzc < 0:
+// all planes; f and u always point at plane 0).
+static pp_status run_stage(pp_plan* p, int stage, const void* f, void* u, int transpose, cudaStream_t st,
+                           int z0 = 0, int nzc = -1) {
   int io = (p->dtype == PP_MIXED_F32IO) ? ST_F32 : ST_F64;
   cudaError_t e = cudaSuccess;
   static const char* names[] = {"x-forward", "y-forward", "z-solve", "y-inverse", "x-inverse"};
   switch (stage) {
-    case 0: e = launch_lines(p, 0, 0, io, ST_SPILL, f, p->bufA, st); break;
-    case 1: e = launch_lines(p, 1, 0, ST_SPILL, ST_SPILL, p->bufA, p->bufB, st); break;
+    case 0: e = launch_lines(p, 0, 0, io, ST_SPILL, f, p->bufA, st, z0, nzc); break;
+    case 1: e = launch_lines(p, 1, 0, ST_SPILL, ST_SPILL, p->bufA, p->bufB, st, z0, nzc); break;
     case 2: e = launch_zsolve(p, p->bufB, transpose, st); break;
-    case 3: e = launch_lines(p, 1, 1, ST_SPILL, ST_SPILL, p->bufB, p->bufA, st); break;
-    case 4: e = launch_lines(p, 0, 1, ST_SPILL, io, p->bufA, u, st); break;
+    case 3: e = launch_lines(p, 1, 1, ST_SPILL, ST_SPILL, p->bufB, p->bufA, st, z0, nzc); break;
+    case 4: e = launch_lines(p, 0, 1, ST_SPILL, io, p->bufA, u, st, z0, nzc); break;
     default: return fail(PP_ERR_INVALID_ARG, "stage %d out of range", stage);
   }
   if (e != cudaSuccess) return fail(PP_ERR_CUDA, "%s launch: %s", names[stage], cudaGetErrorString(e));
@@ -991,18 +1011,59 @@ pp_status pp_solve_batched(pp_plan* const* plans, const void* const* f, void* co
 
 pp_status pp_solve_host(pp_plan* p, const void* f_host, void* u_host, pp_stream_t stream) {
   if (!p || !f_host || !u_host) return fail(PP_ERR_INVALID_ARG, "NULL plan or pointer");
-  size_t bytes = (size_t)p->nx * p->ny * p->nz * (p->dtype == PP_MIXED_F32IO ? 4 : 8);
+  const size_t elem = (p->dtype == PP_MIXED_F32IO ? 4 : 8);
+  const size_t plane = (size_t)p->nx * p->ny * elem;
+  const size_t bytes = plane * p->nz;
   if (!p->d_host_f) {
     cudaError_t e = cudaMalloc(&p->d_host_f, bytes);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_host_u, bytes);
     if (e != cudaSuccess) return fail(PP_ERR_OUT_OF_MEMORY, "staging buffers: %s", cudaGetErrorString(e));
   }
+  if (!p->host_cs[0]) {
+    for (cudaStream_t& s : p->host_cs) CUDA_OK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    for (cudaEvent_t& e : p->host_ev) CUDA_OK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  // Plane chunks: the host->device copy of chunk c (copy engines, two streams) overlaps the x/y
+  // forward transforms of the chunks before it; after the z solve, the device->host copy of
+  // chunk c overlaps the inverse transforms of the chunks after it.
   cudaStream_t st = (cudaStream_t)stream;
-  CUDA_OK(cudaMemcpyAsync(p->d_host_f, f_host, bytes, cudaMemcpyHostToDevice, st));
-  pp_status s = run_pipeline(p, p->d_host_f, p->d_host_u, 0, st);
+  cudaEvent_t* ev = p->host_ev;
+  const int C = std::min(kHostChunks, p->nz);
+  auto z0 = [&](int c) { return (int)((long long)c * p->nz / C); };
+  char* df = static_cast<char*>(p->d_host_f);
+  char* du = static_cast<char*>(p->d_host_u);
+  CUDA_OK(cudaEventRecord(ev[2 * kHostChunks], st));  // earlier work on st (users of the staging buffers)
+  for (cudaStream_t s : p->host_cs) CUDA_OK(cudaStreamWaitEvent(s, ev[2 * kHostChunks], 0));
+  for (int c = 0; c < C; c++) {
+    const size_t off = (size_t)z0(c) * plane, n = (size_t)(z0(c + 1) - z0(c)) * plane;
+    CUDA_OK(cudaMemcpyAsync(df + off, static_cast<const char*>(f_host) + off, n, cudaMemcpyHostToDevice, p->host_cs[c % 2]));
+    CUDA_OK(cudaEventRecord(ev[c], p->host_cs[c % 2]));
+  }
+  for (int c = 0; c < C; c++) {
+    CUDA_OK(cudaStreamWaitEvent(st, ev[c], 0));
+    for (int stage : {0, 1}) {
+      pp_status s = run_stage(p, stage, df, du, 0, st, z0(c), z0(c + 1) - z0(c));
+      if (s != PP_OK) return s;
+    }
+  }
+  pp_status s = run_stage(p, 2, df, du, 0, st);
   if (s != PP_OK) return s;
-  CUDA_OK(cudaMemcpyAsync(u_host, p->d_host_u, bytes, cudaMemcpyDeviceToHost, st));
+  for (int c = 0; c < C; c++) {
+    for (int stage : {3, 4}) {
+      s = run_stage(p, stage, df, du, 0, st, z0(c), z0(c + 1) - z0(c));
+      if (s != PP_OK) return s;
+    }
+    CUDA_OK(cudaEventRecord(ev[kHostChunks + c], st));
+    CUDA_OK(cudaStreamWaitEvent(p->host_cs[c % 2], ev[kHostChunks + c], 0));
+    const size_t off = (size_t)z0(c) * plane, n = (size_t)(z0(c + 1) - z0(c)) * plane;
+    CUDA_OK(cudaMemcpyAsync(static_cast<char*>(u_host) + off, du + off, n, cudaMemcpyDeviceToHost, p->host_cs[c % 2]));
+  }
+  for (int k = 0; k < 2; k++) {
+    CUDA_OK(cudaEventRecord(ev[2 * kHostChunks + 1 + k], p->host_cs[k]));
+    CUDA_OK(cudaStreamWaitEvent(st, ev[2 * kHostChunks + 1 + k], 0));
+  }
   CUDA_OK(cudaStreamSynchronize(st));
+  (void)bytes;
   return PP_OK;
 }
 

@@ -125,6 +125,23 @@ def test_host_buffers(oracle):
     plan.close()
 
 
+@pytest.mark.parametrize("shape,bc,dtype,tol", [((13, 12, 16), "NNDDPP", "f64", TOL_F64),     # 8 uneven plane chunks
+                                                 ((5, 8, 24), "DDPPNN", "f64", TOL_F64),       # fewer planes than chunks
+                                                 ((2, 6, 8), "PPNNDD", "mixed_f64io", 1e-6),
+                                                 ((11, 16, 12), "DNNDND", "mixed_f32io", 1e-5)])
+def test_host_buffers_chunked(oracle, shape, bc, dtype, tol):
+    """Host-buffer solves copy and transform in plane chunks; every chunk size and dtype."""
+    import paper_1909_05423_gb300 as pp
+    f = workloads.uniform_source(shape, seed=16)
+    plan = pp.Plan(shape, bc, (1, 1, 1), dtype)
+    fh = torch.from_numpy(f).to(plan.io_dtype).pin_memory()
+    ref = oracle.solve(fh.double().numpy(), bc)
+    for _ in range(2):  # the second call reuses the staging buffers and streams
+        u = plan.solve_host(fh)
+        assert rel_l2(u.double().numpy(), ref) <= tol
+    plan.close()
+
+
 def test_batched_uneven(oracle):
     """Uneven sizes and boundary sets in one batched call (each against its own oracle solve)."""
     import paper_1909_05423_gb300 as pp
