@@ -405,6 +405,7 @@ def run_ours(args):
     clk = clocks.stop()
     ms_all, value = replica_aggregate(ms, npts, dist, device="cuda")
     plan.status()
+    shapes = {k: {"threads": t, "lines_per_cta": l} for k, (t, l) in plan.launch_shapes().items()}
 
     # roofline of the dominant kernel: algorithmic bytes = read input once + write output once
     elem = 8  # FP64 I/O and double-float spill: 8 bytes per real
@@ -499,7 +500,8 @@ def run_ours(args):
             "config": {"workload": "%d^3 FP64 Neumann-x/Dirichlet-y/Neumann-z, U[-1,1] source" % n, "bc": BC,
                        "n": n, "points": npts, "l2": "inputs (8 GiB/grid) exceed L2; no flush",
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "stage_ms": dict(zip(STAGES, per)), "path_hbm_gbs_32B_per_point": path_gbs,
+                       "stage_ms": dict(zip(STAGES, per)), "launch_shapes": shapes,
+                       "path_hbm_gbs_32B_per_point": path_gbs,
                        "path_hbm_frac_32B_per_point": path_gbs / peak},
             "roofline": roof,
             "kernels": per_stage,

@@ -197,6 +197,12 @@ pp_status pp_plan_status(pp_plan* plan);
 /* Bytes of device memory held by the plan (workspace + tables). */
 size_t pp_plan_device_bytes(const pp_plan* plan);
 
+/* Launch shapes the plan uses (heuristic or autotuned): out[8] receives threads per CTA and lines
+ * per CTA of the x-forward, y-forward, y-inverse and x-inverse kernels, in that order (for the y
+ * kernels, real lines: two per complex column when its parts are transformed separately).
+ * Errors: PP_ERR_INVALID_ARG (NULL). */
+pp_status pp_plan_launch_shapes(const pp_plan* plan, int out[8]);
+
 /* Human-readable detail of the last error on the calling thread ("" if none). */
 const char* pp_last_error_string(void);
 

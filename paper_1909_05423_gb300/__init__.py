@@ -149,6 +149,13 @@ class Plan:
     def device_bytes(self) -> int:
         return int(_lib.load().pp_plan_device_bytes(self._h))
 
+    def launch_shapes(self) -> dict:
+        """(threads per CTA, lines per CTA) of the four line kernels."""
+        v = (ctypes.c_int * 8)()
+        _lib.check(_lib.load().pp_plan_launch_shapes(self._h, v))
+        names = ["x-forward", "y-forward", "y-inverse", "x-inverse"]
+        return {k: (v[2 * i], v[2 * i + 1]) for i, k in enumerate(names)}
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             _lib.load().pp_plan_destroy(self._h)

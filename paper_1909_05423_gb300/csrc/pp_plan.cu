@@ -1082,6 +1082,14 @@ pp_status pp_plan_status(pp_plan* p) {
   return PP_OK;
 }
 
+pp_status pp_plan_launch_shapes(const pp_plan* p, int out[8]) {
+  if (!p || !out) return fail(PP_ERR_INVALID_ARG, "NULL plan or pointer");
+  const int v[8] = {p->threads_x[0], p->lpc_x[0], p->threads_y[0], p->lpc_y[0],
+                    p->threads_y[1], p->lpc_y[1], p->threads_x[1], p->lpc_x[1]};
+  for (int i = 0; i < 8; i++) out[i] = v[i];
+  return PP_OK;
+}
+
 size_t pp_plan_device_bytes(const pp_plan* p) {
   if (!p) return 0;
   return 2 * p->buf_bytes;

@@ -219,6 +219,21 @@ def test_autotuned_plan_matches_oracle(oracle):
         assert rel_l2(u, ref) <= TOL_F64
 
 
+def test_launch_shapes_and_overrides():
+    """Reported launch shapes obey the capacity rule (lines x FFT length <= 8 x threads), and
+    per-direction overrides reach the inverse kernels only."""
+    import paper_1909_05423_gb300 as pp
+    shape = (8, 48, 64)  # x: NN -> M = 32, y: DD -> M = 24
+    plan = pp.Plan(shape, "NNDDPP", (1, 1, 1), "f64", options={"threads_x_inv": 256, "lines_x_inv": 3})
+    sh = plan.launch_shapes()
+    M = {"x-forward": 32, "x-inverse": 32, "y-forward": 24, "y-inverse": 24}
+    for k, (t, l) in sh.items():
+        assert t % 32 == 0 and 32 <= t <= 512 and l >= 1 and l * M[k] <= 8 * t, (k, t, l)
+    assert sh["x-inverse"] == (256, 3)
+    assert sh["x-forward"][0] == 128  # the default CTA size
+    plan.close()
+
+
 def test_fault_injection_graph(oracle, monkeypatch):
     """An injected graph-instantiation failure surfaces as PP_ERR_CUDA from pp_solve_batched; the
     plans stay usable and the next batch (injection off) is correct."""
