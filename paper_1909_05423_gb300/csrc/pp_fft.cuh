@@ -56,6 +56,16 @@ template <> struct NBut<8> { static constexpr int v = 1; };
 constexpr int kCapPerThread = 8;
 constexpr int kCapPerThread3 = 8;
 
+// Compile-time lengths transform every line with its own team of MC/VPT consecutive threads, VPT
+// (8 or 16) complex values per thread per stage.  Teams of up to one warp synchronise their stages
+// with the warp alone; wider teams use the CTA barrier.  The y kernels of 512-point lines use
+// VPT = 16 (one warp per line; measured faster), every other kernel VPT = 8.
+constexpr int ct_values_per_thread(int MC, bool y_lines) { return (MC == 512 && y_lines) ? 16 : 8; }
+template <int TPL> __device__ __forceinline__ void team_sync() {
+  if constexpr (TPL <= 32) __syncwarp();
+  else __syncthreads();
+}
+
 // r-point DFTs in registers (forward kernel exp(-2 pi i/r); INV uses the conjugate).
 template <class R, bool INV> __device__ __forceinline__ void dft2(cx<R>* a) {
   cx<R> t = a[0];
@@ -252,28 +262,28 @@ __device__ __forceinline__ void fft_lines(cx<R>* buf, int nlines, int ldm, const
 // telescope), and the last stage (p = 0, all twiddles 1) keeps none.
 template <int REM> struct CtRadix { static constexpr int v = (REM % 8 == 0) ? 8 : (REM % 4 == 0 ? 4 : 2); };
 
-template <class R, int RAD, bool INV, int MC, int S, int TWOFF>
+template <class R, int RAD, bool INV, int MC, int VPT, int S, int TWOFF>
 __device__ __forceinline__ void fft_stage_ct(cx<R>* buf, int nlines, int ldm, const cx<R>* tw) {
-  constexpr int NB = NBut<RAD>::v;
   constexpr int nbl = MC / RAD;
-  const int total = nlines * nbl;
+  constexpr int TPL = MC / VPT;
+  constexpr int NB = nbl / TPL;  // butterflies per thread
+  static_assert(NB * TPL == nbl && NB * RAD <= 16, "team covers the line");
+  const int line = (int)threadIdx.x / TPL, lt = (int)threadIdx.x % TPL;
+  const bool act = line < nlines;
   cx<R> a[NB][RAD];
+  if (act) {
 #pragma unroll
-  for (int i = 0; i < NB; i++) {
-    const int b = threadIdx.x + i * blockDim.x;
-    if (b < total) {
-      const int line = b / nbl, j = b % nbl;
-      const cx<R>* x = buf + line * ldm + pad(j);
+    for (int i = 0; i < NB; i++) {
+      const cx<R>* x = buf + line * ldm + pad(lt + i * TPL);
 #pragma unroll
       for (int u = 0; u < RAD; u++) a[i][u] = x[u * nbl + ((u * nbl) >> 5)];
     }
   }
-  __syncthreads();
+  team_sync<TPL>();
 #pragma unroll
   for (int i = 0; i < NB; i++) {
-    const int b = threadIdx.x + i * blockDim.x;
-    if (b < total) {
-      const int line = b / nbl, j = b % nbl;
+    if (act) {
+      const int j = lt + i * TPL;
       const int p = j / S, q = j % S;
       dft_r<R, RAD, INV>(a[i]);
       cx<R>* y = buf + line * ldm + pad(q + S * RAD * p);
@@ -290,66 +300,74 @@ __device__ __forceinline__ void fft_stage_ct(cx<R>* buf, int nlines, int ldm, co
       }
     }
   }
-  __syncthreads();
+  team_sync<TPL>();
 }
 
 // tw: the per-stage table of load_stage_twiddles
-template <class R, bool INV, int MC, int S, int TWOFF = 0>
+template <class R, bool INV, int MC, int VPT, int S = 1, int TWOFF = 0>
 __device__ __forceinline__ void fft_lines_ct(cx<R>* buf, int nlines, int ldm, const cx<R>* tw) {
   if constexpr (S < MC) {
     constexpr int RAD = CtRadix<MC / S>::v;
-    fft_stage_ct<R, RAD, INV, MC, S, TWOFF>(buf, nlines, ldm, tw);
+    fft_stage_ct<R, RAD, INV, MC, VPT, S, TWOFF>(buf, nlines, ldm, tw);
     constexpr int NEXT = (S * RAD < MC) ? TWOFF + (MC / (S * RAD)) * (RAD - 1) : TWOFF;
-    fft_lines_ct<R, INV, MC, S * RAD, NEXT>(buf, nlines, ldm, tw);
+    fft_lines_ct<R, INV, MC, VPT, S * RAD, NEXT>(buf, nlines, ldm, tw);
   }
 }
 
-// Radix-8 stage with the stride S = 2^lgS known only at run time (one butterfly per thread).  The
+// Radix-8 stage with the stride S = 2^lgS known only at run time (line teams as above).  The
 // double-float butterfly is long (~900 instructions); running all radix-8 stages through one copy
 // of it keeps the kernel's hot code within the instruction cache.  Same addressing and twiddle
 // table as fft_stage_ct (radix-8 stages come first, so this stage's twiddles start at MC - MC/S).
-template <class R, bool INV, int MC>
+template <class R, bool INV, int MC, int VPT>
 __device__ __forceinline__ void fft_stage8_rt(cx<R>* buf, int nlines, int ldm, const cx<R>* tw, int lgS, bool last) {
   constexpr int nbl = MC / 8;
-  const int total = nlines * nbl;
-  const int b = threadIdx.x;
-  const int line = b / nbl, j = b % nbl;
-  cx<R> a[8];
-  const bool act = b < total;
+  constexpr int TPL = MC / VPT;
+  constexpr int NB = nbl / TPL;  // butterflies per thread
+  const int line = (int)threadIdx.x / TPL, lt = (int)threadIdx.x % TPL;
+  const bool act = line < nlines;
+  cx<R> a[NB][8];
   if (act) {
-    const cx<R>* x = buf + line * ldm + pad(j);
 #pragma unroll
-    for (int u = 0; u < 8; u++) a[u] = x[u * nbl + ((u * nbl) >> 5)];
-  }
-  __syncthreads();
-  if (act) {
-    const int p = j >> lgS, q = j & ((1 << lgS) - 1);
-    dft8<R, INV>(a);
-    cx<R>* y = buf + line * ldm + pad(q + ((8 * p) << lgS));
-    y[0] = a[0];
-    if (last) {
+    for (int i = 0; i < NB; i++) {
+      const cx<R>* x = buf + line * ldm + pad(lt + i * TPL);
 #pragma unroll
-      for (int t = 1; t < 8; t++) y[(t << lgS) + ((t << lgS) >> 5)] = a[t];
-    } else {
-      const cx<R>* w = tw + (MC - (MC >> lgS)) + p * 7;
-#pragma unroll
-      for (int t = 1; t < 8; t++)
-        y[(t << lgS) + ((t << lgS) >> 5)] = INV ? cmulc(a[t], w[t - 1]) : cmul(a[t], w[t - 1]);
+      for (int u = 0; u < 8; u++) a[i][u] = x[u * nbl + ((u * nbl) >> 5)];
     }
   }
-  __syncthreads();
+  team_sync<TPL>();
+#pragma unroll
+  for (int i = 0; i < NB; i++) {
+    if (act) {
+      const int j = lt + i * TPL;
+      const int p = j >> lgS, q = j & ((1 << lgS) - 1);
+      dft8<R, INV>(a[i]);
+      cx<R>* y = buf + line * ldm + pad(q + ((8 * p) << lgS));
+      y[0] = a[i][0];
+      if (last) {
+#pragma unroll
+        for (int t = 1; t < 8; t++) y[(t << lgS) + ((t << lgS) >> 5)] = a[i][t];
+      } else {
+        const cx<R>* w = tw + (MC - (MC >> lgS)) + p * 7;
+#pragma unroll
+        for (int t = 1; t < 8; t++)
+          y[(t << lgS) + ((t << lgS) >> 5)] = INV ? cmulc(a[i][t], w[t - 1]) : cmul(a[i][t], w[t - 1]);
+      }
+    }
+  }
+  team_sync<TPL>();
 }
 
 // All stages of a power-of-two length: the radix-8 stages in a loop (not unrolled), then the
 // remaining radix-4 or radix-2 stage.  Same stage sequence and results as fft_lines_ct.
-template <class R, bool INV, int MC>
+template <class R, bool INV, int MC, int VPT>
 __device__ __forceinline__ void fft_lines_lp(cx<R>* buf, int nlines, int ldm, const cx<R>* tw) {
   constexpr int L8 = (MC >= 8) ? (31 - __builtin_clz(MC)) / 3 : 0;
   constexpr int REM = MC >> (3 * L8);
 #pragma unroll 1
-  for (int st = 0; st < L8; st++) fft_stage8_rt<R, INV, MC>(buf, nlines, ldm, tw, 3 * st, REM == 1 && st == L8 - 1);
-  if constexpr (REM == 4) fft_stage_ct<R, 4, INV, MC, MC / 4, 0>(buf, nlines, ldm, tw);
-  if constexpr (REM == 2) fft_stage_ct<R, 2, INV, MC, MC / 2, 0>(buf, nlines, ldm, tw);
+  for (int st = 0; st < L8; st++)
+    fft_stage8_rt<R, INV, MC, VPT>(buf, nlines, ldm, tw, 3 * st, REM == 1 && st == L8 - 1);
+  if constexpr (REM == 4) fft_stage_ct<R, 4, INV, MC, VPT, MC / 4, 0>(buf, nlines, ldm, tw);
+  if constexpr (REM == 2) fft_stage_ct<R, 2, INV, MC, VPT, MC / 2, 0>(buf, nlines, ldm, tw);
 }
 
 }  // namespace pp

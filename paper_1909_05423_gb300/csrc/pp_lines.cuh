@@ -639,13 +639,15 @@ __global__ void __launch_bounds__(512, MinBlocks<R>::v) k_lines(const LineArgs a
   if constexpr (MC > 0) {
     // double-float lines of 512+ complex points: radix-8 stages share one copy of the butterfly
     // (measured faster there; the shorter lengths keep fully compile-time stages)
+    constexpr int VPT = ct_values_per_thread(MC, OY);
     if constexpr (std::is_same<R, df>::value && MC >= 512) {
-      if (inv) fft_lines_lp<R, true, MC>(buf, nl, ldm, tws);
-      else fft_lines_lp<R, false, MC>(buf, nl, ldm, tws);
+      if (inv) fft_lines_lp<R, true, MC, VPT>(buf, nl, ldm, tws);
+      else fft_lines_lp<R, false, MC, VPT>(buf, nl, ldm, tws);
     } else {
-      if (inv) fft_lines_ct<R, true, MC, 1>(buf, nl, ldm, tws);
-      else fft_lines_ct<R, false, MC, 1>(buf, nl, ldm, tws);
+      if (inv) fft_lines_ct<R, true, MC, VPT>(buf, nl, ldm, tws);
+      else fft_lines_ct<R, false, MC, VPT>(buf, nl, ldm, tws);
     }
+    __syncthreads();  // warp teams synchronised only themselves; post-processing reads every line
   } else {
     if (inv) fft_lines<R, true>(buf, nl, ldm, a.fp, tws);
     else fft_lines<R, false>(buf, nl, ldm, a.fp, tws);

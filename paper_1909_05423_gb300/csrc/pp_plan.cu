@@ -367,6 +367,12 @@ static void free_plan(pp_plan* p) {
   delete p;
 }
 
+// Complex values a thread holds per FFT stage: 16 in the y kernels of 512-point lines (one warp per
+// line), 8 in every other kernel (9 for radix 3): lines per CTA x M must not exceed this x threads.
+static int values_per_thread(int M, int axis) {
+  return ct_length(M) ? ct_values_per_thread(M, axis == 1) : kCapPerThread;
+}
+
 // launch shapes: threads per CTA and lines per CTA of the x and y line kernels, per direction
 // (0 forward, 1 inverse).  Shared memory per CTA = the complex work buffer + the stage twiddles.
 static void choose_shapes(pp_plan* p, const pp_plan_options* opt) {
@@ -388,11 +394,12 @@ static void choose_shapes(pp_plan* p, const pp_plan_options* opt) {
       int M = p->fx.M;
       bool r3 = false;
       for (int i = 0; i < p->fx.nst; i++) r3 |= p->fx.rad[i] == 3;
-      // a CTA must hold at least one whole line: threads * kCapPerThread >= M
-      const int tmin = std::max(32, ((M + kCapPerThread - 1) / kCapPerThread + 31) / 32 * 32);
+      // a CTA must hold at least one whole line: threads * (values per thread) >= M
+      const int cpt = values_per_thread(M, 0);
+      const int tmin = std::max(32, ((M + cpt - 1) / cpt + 31) / 32 * 32);
       int T = tx_req ? tx_req : 128;
       T = std::max(T, tmin);
-      int cap = (r3 ? kCapPerThread3 : kCapPerThread) * T;
+      int cap = (r3 ? kCapPerThread3 : cpt) * T;
       int nlines = p->ny * p->nz;
       int lpc = std::max(1, cap / std::max(M, 1));
       if (lx_req) lpc = std::min(lpc, lx_req);
@@ -415,14 +422,15 @@ static void choose_shapes(pp_plan* p, const pp_plan_options* opt) {
       int ncols = cplx_cols ? p->nx / 2 + 1 : p->nx;
       size_t col_bytes = (cplx_cols ? 2 : 1) * se;
       // CTA size: 128 threads unless that leaves column segments below one 32-byte sector
-      const int tmin = std::max(32, ((M + kCapPerThread - 1) / kCapPerThread + 31) / 32 * 32);
+      const int cpt = values_per_thread(M, 1);
+      const int tmin = std::max(32, ((M + cpt - 1) / cpt + 31) / 32 * 32);
       int T = 128;
       const int tmax = 512;
       if (ty_req) T = ty_req;
       else
-        while (T < tmax && (size_t)std::max(1, (kCapPerThread3 * T / std::max(M, 1)) / parts) * col_bytes < 32) T *= 2;
+        while (T < tmax && (size_t)std::max(1, (cpt * T / std::max(M, 1)) / parts) * col_bytes < 32) T *= 2;
       T = std::max(T, tmin);
-      int cap = (r3 ? kCapPerThread3 : kCapPerThread) * T;
+      int cap = (r3 ? kCapPerThread3 : cpt) * T;
       int maxlines = std::max(1, cap / std::max(M, 1));
       int cols = std::max(1, maxlines / parts);
       if (cy_req) cols = std::min(cols, cy_req);
@@ -431,7 +439,7 @@ static void choose_shapes(pp_plan* p, const pp_plan_options* opt) {
       // complex columns split into two real lines need room for both
       while (cols * parts * M > cap && T < tmax) {
         T = std::min(2 * T, tmax);
-        cap = (r3 ? kCapPerThread3 : kCapPerThread) * T;
+        cap = (r3 ? kCapPerThread3 : cpt) * T;
       }
       int ldm = M + (M >> 5) + 1;
       auto need = [&](int c) { return (size_t)c * parts * ldm * cs + (size_t)M * cs; };
@@ -502,7 +510,8 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
     out = static_cast<char*>(out) + (size_t)z0 * a.out_plane * st_bytes(p, io_out);
     a.in = in;
     a.out = out;
-    if ((long long)a.lpc * a.fp.M > (long long)kCapPerThread * p->threads_x[dir]) return cudaErrorInvalidConfiguration;
+    if ((long long)a.lpc * a.fp.M > (long long)values_per_thread(a.fp.M, 0) * p->threads_x[dir])
+      return cudaErrorInvalidConfiguration;
     a.ntiles = (a.nlines + a.lpc - 1) / a.lpc;
     a.vec_ok = (((uintptr_t)in | (uintptr_t)out) % 32 == 0) ? 1 : 0;
     a.fd_gpc = FastDiv::make(1u);
@@ -541,7 +550,8 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
   out = static_cast<char*>(out) + (size_t)z0 * a.out_plane * st_bytes(p, io_out);
   a.in = in;
   a.out = out;
-  if ((long long)a.lpc * a.fp.M > (long long)kCapPerThread * p->threads_y[dir]) return cudaErrorInvalidConfiguration;
+  if ((long long)a.lpc * a.fp.M > (long long)values_per_thread(a.fp.M, 1) * p->threads_y[dir])
+    return cudaErrorInvalidConfiguration;
   a.tx = a.lpc / parts;
   a.ncols = ncols;
   a.nblk = (ncols + a.tx - 1) / a.tx;
