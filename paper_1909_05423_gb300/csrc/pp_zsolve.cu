@@ -40,11 +40,12 @@ __device__ __forceinline__ df f2df(const float* v) { return df{v[0], v[1]}; }
 __device__ __forceinline__ df f2df(float2 v) { return df{v.x, v.y}; }
 
 // Planes per batch.  Each sweep loads the next batch before it computes the current one, so a
-// thread always has one batch of loads in flight (the sweeps are bound by loads in flight).
-constexpr int ZU = 8;
+// thread always has one batch of loads in flight (the sweeps are bound by loads in flight): 8
+// double-float planes (64 bytes), 16 FP32 planes (64 bytes).
+template <class S> struct ZBatch { static constexpr int v = (sizeof(S) == 4) ? 16 : 8; };
 
 // raw values of planes k0 + step*u, u < ZU, that lie in [0, n)
-template <class S>
+template <int ZU, class S>
 __device__ __forceinline__ void zload(S* v, const S* base, long long P, int k0, int step, int n) {
 #pragma unroll
   for (int u = 0; u < ZU; u++) {
@@ -107,6 +108,7 @@ __global__ void __launch_bounds__(256) k_zsolve(const ZArgs a) {
     if (k < wlen) return f2df(__ldg(wt + k));
     return winf;
   };
+  constexpr int ZU = ZBatch<S>::v;
   S cur[ZU], nxt[ZU];
 
   if constexpr (MODE != 2) {
@@ -116,9 +118,9 @@ __global__ void __launch_bounds__(256) k_zsolve(const ZArgs a) {
     // forward elimination g_k = (s d_k - g_{k-1}) w_k; periodic: y0 = sum q_k s d_k
     df g = df{0.f, 0.f};
     df y0 = df{0.f, 0.f};
-    zload(cur, base, P, 0, 1, n);
+    zload<ZU>(cur, base, P, 0, 1, n);
     for (int k0 = 0; k0 < n; k0 += ZU) {
-      if (k0 + ZU < n) zload(nxt, base, P, k0 + ZU, 1, n);
+      if (k0 + ZU < n) zload<ZU>(nxt, base, P, k0 + ZU, 1, n);
 #pragma unroll
       for (int u = 0; u < ZU; u++) {
         const int k = k0 + u;
@@ -140,9 +142,9 @@ __global__ void __launch_bounds__(256) k_zsolve(const ZArgs a) {
     }
     df u = df{0.f, 0.f};
     df p = wlast;
-    zload(cur, base, P, n - 1, -1, n);
+    zload<ZU>(cur, base, P, n - 1, -1, n);
     for (int k0 = n - 1; k0 >= 0; k0 -= ZU) {
-      if (k0 - ZU >= 0) zload(nxt, base, P, k0 - ZU, -1, n);
+      if (k0 - ZU >= 0) zload<ZU>(nxt, base, P, k0 - ZU, -1, n);
 #pragma unroll
       for (int t = 0; t < ZU; t++) {
         const int k = k0 - t;
@@ -167,9 +169,9 @@ __global__ void __launch_bounds__(256) k_zsolve(const ZArgs a) {
     // transposed factorisation T^T = U^T L^T:  h_k = s d_k - w_{k-1} h_{k-1},  x_k = (h_k - x_{k+1}) w_k
     df h = df{0.f, 0.f};
     df wprev = df{0.f, 0.f};
-    zload(cur, base, P, 0, 1, n);
+    zload<ZU>(cur, base, P, 0, 1, n);
     for (int k0 = 0; k0 < n; k0 += ZU) {
-      if (k0 + ZU < n) zload(nxt, base, P, k0 + ZU, 1, n);
+      if (k0 + ZU < n) zload<ZU>(nxt, base, P, k0 + ZU, 1, n);
 #pragma unroll
       for (int u = 0; u < ZU; u++) {
         const int k = k0 + u;
@@ -184,9 +186,9 @@ __global__ void __launch_bounds__(256) k_zsolve(const ZArgs a) {
       for (int u = 0; u < ZU; u++) cur[u] = nxt[u];
     }
     df x = df{0.f, 0.f};
-    zload(cur, base, P, n - 1, -1, n);
+    zload<ZU>(cur, base, P, n - 1, -1, n);
     for (int k0 = n - 1; k0 >= 0; k0 -= ZU) {
-      if (k0 - ZU >= 0) zload(nxt, base, P, k0 - ZU, -1, n);
+      if (k0 - ZU >= 0) zload<ZU>(nxt, base, P, k0 - ZU, -1, n);
 #pragma unroll
       for (int t = 0; t < ZU; t++) {
         const int k = k0 - t;
