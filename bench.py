@@ -343,9 +343,10 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     n = args.n
-    shape = (n, n, n)
-    sp = (1.0 / n,) * 3
-    npts = n ** 3
+    shape = tuple(int(v) for v in args.shape.split(",")) if args.shape else (n, n, n)
+    nz_, ny_, nx_ = shape
+    sp = (1.0 / nx_, 1.0 / ny_, 1.0 / nz_)
+    npts = nx_ * ny_ * nz_
     lib = _lib.load()
 
     # input: seeded U[-1,1], mean removed, generated on the device
@@ -409,7 +410,7 @@ def run_ours(args):
 
     # roofline of the dominant kernel: algorithmic bytes = read input once + write output once
     elem = 8  # FP64 I/O and double-float spill: 8 bytes per real
-    xs = (n + 2) / n if BC[0] == "P" else 1.0
+    xs = (nx_ + 2) / nx_ if BC[0] == "P" else 1.0
     alg_bytes = {"x-forward": npts * elem * (1 + xs), "y-forward": 2 * npts * elem * xs,
                  "z-solve": 2 * npts * elem * xs, "y-inverse": 2 * npts * elem * xs,
                  "x-inverse": npts * elem * (1 + xs)}
@@ -426,7 +427,7 @@ def run_ours(args):
         d = {"ms": per[k], "hbm_gbs": alg_bytes[name] / (per[k] * 1e-3) / 1e9}
         d["hbm_frac"] = d["hbm_gbs"] / peak
         if name in kinds:
-            opr = line_ops_per_real(kinds[name], n, "df")
+            opr = line_ops_per_real(kinds[name], nx_ if name[0] == "x" else ny_, "df")
             d["fp32_ops_per_point"] = opr
             d["alu_tops"] = opr * npts / (per[k] * 1e-3) / 1e12
             d["alu_frac"] = d["alu_tops"] / alu_peak
@@ -437,11 +438,11 @@ def run_ours(args):
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz; FP32 operations counted as "
                                "issued lane instructions (FMA = 1)",
                 "alg_fp32_ops_per_point": per_stage[dname]["fp32_ops_per_point"],
-                "hbm_frac": per_stage[dname]["hbm_frac"], "traffic": _traffic(dname, n),
+                "hbm_frac": per_stage[dname]["hbm_frac"], "traffic": None if args.shape else _traffic(dname, n),
                 "alg_bytes_per_launch": alg_bytes[dname]}
     else:
         roof = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_kind, "traffic": _traffic(dname, n),
+                "frac": achieved / peak, "peak_source": peak_kind, "traffic": None if args.shape else _traffic(dname, n),
                 "alg_bytes_per_launch": alg_bytes[dname]}
 
     # ---------------------------------------------------------------- mixed precision variants
@@ -497,8 +498,10 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64 I/O, double-float (2xf32) transforms and z-solve",
             "data": "synthetic (seeded U[-1,1], mean removed; generated on device)",
-            "config": {"workload": "%d^3 FP64 Neumann-x/Dirichlet-y/Neumann-z, U[-1,1] source" % n, "bc": BC,
-                       "n": n, "points": npts, "l2": "inputs (8 GiB/grid) exceed L2; no flush",
+            "config": {"workload": "%s FP64 Neumann-x/Dirichlet-y/Neumann-z, U[-1,1] source" %
+                                   ("%d^3" % n if not args.shape else "%dx%dx%d (nz x ny x nx)" % shape), "bc": BC,
+                       "n": n, "shape_zyx": list(shape), "points": npts,
+                       "l2": "inputs (%.1f GiB/grid) exceed L2; no flush" % (npts * 8 / 2 ** 30),
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "stage_ms": dict(zip(STAGES, per)), "launch_shapes": shapes,
                        "path_hbm_gbs_32B_per_point": path_gbs,
@@ -524,6 +527,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--shape", default=None, help="nz,ny,nx of a non-cubic grid (profiling captures; overrides --n)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--oracle-planes", type=int, default=8)
     ap.add_argument("--no-mixed", action="store_true")
