@@ -42,19 +42,22 @@ struct FastDiv {
   }
 };
 
-// butterflies per thread per stage (NB * radix >= 8 for every radix)
+// butterflies per thread per stage
 template <int RAD> struct NBut;
 template <> struct NBut<2> { static constexpr int v = 4; };
-template <> struct NBut<3> { static constexpr int v = 3; };
+template <> struct NBut<3> { static constexpr int v = 2; };
 template <> struct NBut<4> { static constexpr int v = 2; };
-template <> struct NBut<5> { static constexpr int v = 2; };
-template <> struct NBut<7> { static constexpr int v = 2; };
+template <> struct NBut<5> { static constexpr int v = 1; };
+template <> struct NBut<7> { static constexpr int v = 1; };
 template <> struct NBut<8> { static constexpr int v = 1; };
-// complex values a thread holds per stage: 8 for radix 2/4/8, 9 / 10 / 14 for radix 3 / 5 / 7.  A
-// launch is valid only if lines_per_cta * M <= kCapPerThread * threads (checked on the host before
-// every launch): then no stage has more butterflies than NB * threads.
+// complex values a thread holds per stage: 8 for radix 2/4/8, 6 / 5 / 7 for radix 3 / 5 / 7 (few
+// enough registers for the double-float butterflies).  A launch of a run-time-length kernel is
+// valid only if lines_per_cta * M <= (the smallest of these over the line's stages) * threads
+// (checked on the host before every launch): then no stage has more butterflies than NB * threads.
+__host__ __device__ constexpr int stage_capacity(int rad) {
+  return rad == 2 ? 8 : rad == 3 ? 6 : rad == 4 ? 8 : rad == 5 ? 5 : rad == 7 ? 7 : 8;
+}
 constexpr int kCapPerThread = 8;
-constexpr int kCapPerThread3 = 8;
 
 // Compile-time lengths transform every line with its own team of MC/VPT consecutive threads, VPT
 // (8 or 16) complex values per thread per stage.  Teams of up to one warp synchronise their stages

@@ -599,20 +599,26 @@ __device__ __noinline__ void post_tile(const LineArgs& a, const cx<R>* buf, int 
   }
 }
 
-// Residency target: FP32 kernels aim at two 512-thread CTAs per SM (<= 64 registers), the
-// double-float ones at one (<= 128 registers, their butterflies need them).
-template <class R> struct MinBlocks { static constexpr int v = std::is_same<R, float>::value ? 2 : 1; };
+// Register caps: FP32 kernels 64 (two 512-thread CTAs per SM); double-float compile-time-length
+// kernels 80 (six 128-thread CTAs per SM; their butterflies fit without spilling), except the
+// warp-per-line y kernels of 512-point lines (16 values per thread) and the run-time-length
+// kernels (radix-3/5/7 butterflies), which get 128.
+template <class R, bool WIDE> struct MaxRegs {
+  static constexpr int v = std::is_same<R, float>::value ? 64 : (WIDE ? 128 : 80);
+};
 
 // One tile per CTA (x: lpc consecutive rows; y: one plane x tx columns).
 template <class R, class SI, class SO, bool OY, int MC>
-__global__ void __launch_bounds__(512, MinBlocks<R>::v) k_lines(const LineArgs args) {
+__global__ void __maxnreg__((MaxRegs<R, (OY && MC == 512) || MC == 0>::v)) k_lines(const LineArgs args) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ long long s_bin[kMaxLpc], s_bout[kMaxLpc];
   const LineArgs& a = args;
   const int M = MC ? MC : a.fp.M;
   const int ldm = a.ldm;
   cx<R>* buf = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* tws = buf + (size_t)a.lpc * ldm;
+  // per-line base offsets of the tile (input, output), after the twiddles
+  long long* s_bin = reinterpret_cast<long long*>(tws + M);
+  long long* s_bout = s_bin + a.lpc;
   const cx<R>* twg = reinterpret_cast<const cx<R>*>(a.tw);
   // stage twiddles: w_M^j, j < M (run-time lengths) or the per-stage table of fft_lines_ct
   for (int i = threadIdx.x; i < M; i += blockDim.x) tws[i] = twg[i];
@@ -666,7 +672,7 @@ cudaError_t launch_lines_k(const LineArgs& a, int threads, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const size_t sm = ((size_t)a.lpc * a.ldm + (size_t)a.fp.M) * sizeof(cx<R>);
+  const size_t sm = ((size_t)a.lpc * a.ldm + (size_t)a.fp.M) * sizeof(cx<R>) + 2 * (size_t)a.lpc * sizeof(long long);
   k<<<a.ntiles, threads, sm, st>>>(a);
   return cudaGetLastError();
 }

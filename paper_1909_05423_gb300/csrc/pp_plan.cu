@@ -368,13 +368,18 @@ static void free_plan(pp_plan* p) {
 }
 
 // Complex values a thread holds per FFT stage: 16 in the y kernels of 512-point lines (one warp per
-// line), 8 in every other kernel (9 for radix 3): lines per CTA x M must not exceed this x threads.
-static int values_per_thread(int M, int axis) {
-  return ct_length(M) ? ct_values_per_thread(M, axis == 1) : kCapPerThread;
+// line), 8 in the other compile-time-length kernels, and for run-time lengths the smallest stage
+// capacity of the line's radices: lines per CTA x M must not exceed this x threads.
+static int values_per_thread(const FftPlan& fp, int axis) {
+  if (ct_length(fp.M)) return ct_values_per_thread(fp.M, axis == 1);
+  int c = kCapPerThread;
+  for (int i = 0; i < fp.nst; i++) c = std::min(c, stage_capacity(fp.rad[i]));
+  return c;
 }
 
 // launch shapes: threads per CTA and lines per CTA of the x and y line kernels, per direction
-// (0 forward, 1 inverse).  Shared memory per CTA = the complex work buffer + the stage twiddles.
+// (0 forward, 1 inverse).  Shared memory per CTA = the complex work buffer + the stage twiddles +
+// two 8-byte line bases per line.
 static void choose_shapes(pp_plan* p, const pp_plan_options* opt) {
   size_t cs = (p->dtype == PP_F64) ? 16 : 8;          // bytes per complex in shared memory
   size_t se = p->elem;                                  // bytes per spill real
@@ -392,21 +397,19 @@ static void choose_shapes(pp_plan* p, const pp_plan_options* opt) {
     // x lines: a staged tile holds lpc rows of the wider of (grid row, spectral row)
     {
       int M = p->fx.M;
-      bool r3 = false;
-      for (int i = 0; i < p->fx.nst; i++) r3 |= p->fx.rad[i] == 3;
       // a CTA must hold at least one whole line: threads * (values per thread) >= M
-      const int cpt = values_per_thread(M, 0);
+      const int cpt = values_per_thread(p->fx, 0);
       const int tmin = std::max(32, ((M + cpt - 1) / cpt + 31) / 32 * 32);
       int T = tx_req ? tx_req : 128;
       T = std::max(T, tmin);
-      int cap = (r3 ? kCapPerThread3 : cpt) * T;
+      int cap = cpt * T;
       int nlines = p->ny * p->nz;
       int lpc = std::max(1, cap / std::max(M, 1));
       if (lx_req) lpc = std::min(lpc, lx_req);
       lpc = std::min(lpc, kMaxLpc);
       lpc = std::min(lpc, nlines);
       int ldm = M + (M >> 5) + 1;  // one padding slot per 32 elements (see pad() in pp_fft.cuh)
-      auto need = [&](int l) { return (size_t)l * ldm * cs + (size_t)M * cs; };
+      auto need = [&](int l) { return (size_t)l * ldm * cs + (size_t)M * cs + 16 * (size_t)l; };
       while (lpc > 1 && need(lpc) > smem_cap) lpc--;
       p->threads_x[dir] = T;
       p->lpc_x[dir] = lpc;
@@ -415,14 +418,12 @@ static void choose_shapes(pp_plan* p, const pp_plan_options* opt) {
     // y lines: a staged tile holds up to ny rows of tx columns
     {
       int M = p->fy.M;
-      bool r3 = false;
-      for (int i = 0; i < p->fy.nst; i++) r3 |= p->fy.rad[i] == 3;
       bool cplx_cols = (p->layout == 0);
       int parts = (cplx_cols && p->ky != AX_P) ? 2 : 1;
       int ncols = cplx_cols ? p->nx / 2 + 1 : p->nx;
       size_t col_bytes = (cplx_cols ? 2 : 1) * se;
       // CTA size: 128 threads unless that leaves column segments below one 32-byte sector
-      const int cpt = values_per_thread(M, 1);
+      const int cpt = values_per_thread(p->fy, 1);
       const int tmin = std::max(32, ((M + cpt - 1) / cpt + 31) / 32 * 32);
       int T = 128;
       const int tmax = 512;
@@ -430,7 +431,7 @@ static void choose_shapes(pp_plan* p, const pp_plan_options* opt) {
       else
         while (T < tmax && (size_t)std::max(1, (cpt * T / std::max(M, 1)) / parts) * col_bytes < 32) T *= 2;
       T = std::max(T, tmin);
-      int cap = (r3 ? kCapPerThread3 : cpt) * T;
+      int cap = cpt * T;
       int maxlines = std::max(1, cap / std::max(M, 1));
       int cols = std::max(1, maxlines / parts);
       if (cy_req) cols = std::min(cols, cy_req);
@@ -439,10 +440,10 @@ static void choose_shapes(pp_plan* p, const pp_plan_options* opt) {
       // complex columns split into two real lines need room for both
       while (cols * parts * M > cap && T < tmax) {
         T = std::min(2 * T, tmax);
-        cap = (r3 ? kCapPerThread3 : cpt) * T;
+        cap = cpt * T;
       }
       int ldm = M + (M >> 5) + 1;
-      auto need = [&](int c) { return (size_t)c * parts * ldm * cs + (size_t)M * cs; };
+      auto need = [&](int c) { return (size_t)c * parts * ldm * cs + (size_t)M * cs + 16 * (size_t)c * parts; };
       while (cols > 1 && need(cols) > smem_cap) cols--;
       p->threads_y[dir] = T;
       p->lpc_y[dir] = cols * parts;
@@ -510,7 +511,7 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
     out = static_cast<char*>(out) + (size_t)z0 * a.out_plane * st_bytes(p, io_out);
     a.in = in;
     a.out = out;
-    if ((long long)a.lpc * a.fp.M > (long long)values_per_thread(a.fp.M, 0) * p->threads_x[dir])
+    if ((long long)a.lpc * a.fp.M > (long long)values_per_thread(a.fp, 0) * p->threads_x[dir])
       return cudaErrorInvalidConfiguration;
     a.ntiles = (a.nlines + a.lpc - 1) / a.lpc;
     a.vec_ok = (((uintptr_t)in | (uintptr_t)out) % 32 == 0) ? 1 : 0;
@@ -550,7 +551,7 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
   out = static_cast<char*>(out) + (size_t)z0 * a.out_plane * st_bytes(p, io_out);
   a.in = in;
   a.out = out;
-  if ((long long)a.lpc * a.fp.M > (long long)values_per_thread(a.fp.M, 1) * p->threads_y[dir])
+  if ((long long)a.lpc * a.fp.M > (long long)values_per_thread(a.fp, 1) * p->threads_y[dir])
     return cudaErrorInvalidConfiguration;
   a.tx = a.lpc / parts;
   a.ncols = ncols;
