@@ -604,7 +604,7 @@ __device__ __noinline__ void post_tile(const LineArgs& a, const cx<R>* buf, int 
 // warp-per-line y kernels of 512-point lines (16 values per thread) and the run-time-length
 // kernels (radix-3/5/7 butterflies), which get 128.
 template <class R, bool WIDE> struct MaxRegs {
-  static constexpr int v = std::is_same<R, float>::value ? 64 : (WIDE ? 128 : 80);
+  static constexpr int v = std::is_same<R, float>::value ? 64 : (WIDE ? 128 : 64);
 };
 
 // One tile per CTA (x: lpc consecutive rows; y: one plane x tx columns).
