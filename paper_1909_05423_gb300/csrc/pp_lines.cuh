@@ -599,17 +599,17 @@ __device__ __noinline__ void post_tile(const LineArgs& a, const cx<R>* buf, int 
   }
 }
 
-// Register caps: FP32 kernels 64 (two 512-thread CTAs per SM); double-float compile-time-length
-// kernels 80 (six 128-thread CTAs per SM; their butterflies fit without spilling), except the
-// warp-per-line y kernels of 512-point lines (16 values per thread) and the run-time-length
-// kernels (radix-3/5/7 butterflies), which get 128.
-template <class R, bool WIDE> struct MaxRegs {
-  static constexpr int v = std::is_same<R, float>::value ? 64 : (WIDE ? 128 : 64);
+// Register caps (measured; none of these spills): FP32 kernels 64 (two 512-thread CTAs per SM);
+// double-float compile-time-length kernels 64 (eight 128-thread CTAs per SM), except the
+// warp-per-line y kernels of 512-point lines, which hold 16 values per thread (96); the
+// run-time-length kernels (radix-3/5/7 butterflies) get 128.
+template <class R, int MC, bool OY> struct MaxRegs {
+  static constexpr int v = std::is_same<R, float>::value ? 64 : (MC == 0 ? 128 : ((OY && MC == 512) ? 96 : 64));
 };
 
 // One tile per CTA (x: lpc consecutive rows; y: one plane x tx columns).
 template <class R, class SI, class SO, bool OY, int MC>
-__global__ void __maxnreg__((MaxRegs<R, (OY && MC == 512) || MC == 0>::v)) k_lines(const LineArgs args) {
+__global__ void __maxnreg__((MaxRegs<R, MC, OY>::v)) k_lines(const LineArgs args) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const LineArgs& a = args;
   const int M = MC ? MC : a.fp.M;
