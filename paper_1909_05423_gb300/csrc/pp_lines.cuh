@@ -599,12 +599,13 @@ __device__ __noinline__ void post_tile(const LineArgs& a, const cx<R>* buf, int 
   }
 }
 
-// Register caps (measured; none of these spills): FP32 kernels 64 (two 512-thread CTAs per SM);
-// double-float compile-time-length kernels 64 (eight 128-thread CTAs per SM), except the
-// warp-per-line y kernels of 512-point lines, which hold 16 values per thread (96); the
-// run-time-length kernels (radix-3/5/7 butterflies) get 128.
+// Register caps (measured; none of these spills in the compile-time-length kernels): FP32 48
+// (ten 128-thread CTAs per SM); double-float 64 (eight), except the warp-per-line y kernels of
+// 512-point lines, which hold 16 values per thread (96).  The run-time-length kernels (radix-3/5/7
+// butterflies) get 64 (FP32) and 128 (double-float).
 template <class R, int MC, bool OY> struct MaxRegs {
-  static constexpr int v = std::is_same<R, float>::value ? 64 : (MC == 0 ? 128 : ((OY && MC == 512) ? 96 : 64));
+  static constexpr int v = std::is_same<R, float>::value ? (MC == 0 ? 64 : 48)
+                                                         : (MC == 0 ? 128 : ((OY && MC == 512) ? 96 : 64));
 };
 
 // One tile per CTA (x: lpc consecutive rows; y: one plane x tx columns).
