@@ -644,10 +644,10 @@ __global__ void __maxnreg__((MaxRegs<R, MC, OY>::v)) k_lines(const LineArgs args
   pre_tile<R, OY, MC>(a, SrcGlobal<R, SI>{reinterpret_cast<const SI*>(a.in), s_bin, (long long)a.in_pos}, nl, buf);
   __syncthreads();
   if constexpr (MC > 0) {
-    // double-float lines of 512+ complex points: radix-8 stages share one copy of the butterfly
+    // double-float lines of 256+ complex points: radix-8 stages share one copy of the butterfly
     // (measured faster there; the shorter lengths keep fully compile-time stages)
     constexpr int VPT = ct_values_per_thread(MC, OY);
-    if constexpr (std::is_same<R, df>::value && MC >= 512) {
+    if constexpr (std::is_same<R, df>::value && MC >= 256) {
       if (inv) fft_lines_lp<R, true, MC, VPT>(buf, nl, ldm, tws);
       else fft_lines_lp<R, false, MC, VPT>(buf, nl, ldm, tws);
     } else {
