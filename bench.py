@@ -18,6 +18,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -137,7 +138,9 @@ class Clocks:
     def __init__(self, index=0):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % os.getpid())
+        # the raw samples; BENCH_CLOCKS_DIR keeps them (default: the system temporary directory)
+        self.path = os.path.join(os.environ.get("BENCH_CLOCKS_DIR") or tempfile.gettempdir(),
+                                 "bench_clocks_%d.csv" % os.getpid())
 
     def start(self):
         try:
