@@ -57,15 +57,19 @@ def replica_aggregate(ms_local: float, points_local: int, dist=None, device="cpu
     return ms, p.item() / (ms * 1e-3) / 1e9
 
 
+# device-code sources of the solve pipeline (host-side plan code is not part of the hash)
+KERNEL_SOURCES = ("pp_arith.cuh", "pp_fft.cuh", "pp_internal.h", "pp_lines.cuh", "pp_lines.cu", "pp_lines_df_small.cu",
+                  "pp_lines_df_large.cu", "pp_lines_df_any.cu", "pp_lines_f32_small.cu", "pp_lines_f32_large.cu",
+                  "pp_lines_f32_any.cu", "pp_zsolve.cu", "pp_misc.cu")
+
+
 def _source_hash():
     """Hash of the kernel sources (the traffic figures in profiles/ are valid only for these)."""
-    import glob
     import hashlib
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1909_05423_gb300", "csrc", "*"))):
-        if f.endswith((".cu", ".cuh", ".h")):
-            with open(f, "rb") as fh:
-                h.update(fh.read())
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1909_05423_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 

@@ -805,6 +805,9 @@ pp_status pp_plan_create(pp_plan** out, int nx, int ny, int nz, const pp_bc bc[6
     return fail(PP_ERR_UNSUPPORTED_SIZE, "nz = %d out of range (>= 2, periodic z >= 3)", nz);
   if ((long long)nx * ny > (1LL << 30) || (long long)nx * ny * nz > (1LL << 36))
     return fail(PP_ERR_UNSUPPORTED_SIZE, "grid too large");
+  // line counts of one launch are 32-bit: x lines ny*nz, y lines (nx + 2)*nz at most
+  if ((long long)ny * nz >= (1LL << 31) || (long long)(nx + 2) * nz >= (1LL << 31))
+    return fail(PP_ERR_UNSUPPORTED_SIZE, "too many lines per launch (ny*nz and (nx+2)*nz must be < 2^31)");
 
   pp_plan* p = new (std::nothrow) pp_plan();
   if (!p) return fail(PP_ERR_OUT_OF_MEMORY, "host allocation failed");

@@ -51,6 +51,7 @@ def _create(lib, nx, ny, nz, bc, dx=1.0, dtype=0):
     (8, 8, 1, "PPPPDD", 2),      # nz < 2
     (8, 8, 2, "NNNNPP", 2),      # periodic z needs nz >= 3
     (8192, 8, 8, "PPPPDD", 2),   # too long
+    (2, 4096, 1 << 20, "NNNNDD", 2),  # 2^32 x lines in one launch
     (8, 8, 8, "PNPPDD", 3),      # periodic paired with Neumann
     (8, 8, 8, "PPNNDP", 3),
 ])
