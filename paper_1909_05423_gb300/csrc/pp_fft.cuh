@@ -238,7 +238,9 @@ struct FftPlan {
   FastDiv s[kMaxStages];    // product of the earlier radices
 };
 
-template <class R, bool INV>
+// All stages of a run-time length.  R57: the kernel also carries the radix-5 and radix-7
+// butterflies (their registers would otherwise weigh on every 2^a 3^b length).
+template <class R, bool INV, bool R57>
 __device__ __forceinline__ void fft_lines(cx<R>* buf, int nlines, int ldm, const FftPlan& fp, const cx<R>* tw) {
   int s = 1;
   for (int st = 0; st < fp.nst; st++) {
@@ -246,8 +248,8 @@ __device__ __forceinline__ void fft_lines(cx<R>* buf, int nlines, int ldm, const
     if (r == 8) fft_stage<R, 8, INV>(buf, nlines, ldm, s, fp.nbl[st], fp.s[st], tw);
     else if (r == 4) fft_stage<R, 4, INV>(buf, nlines, ldm, s, fp.nbl[st], fp.s[st], tw);
     else if (r == 3) fft_stage<R, 3, INV>(buf, nlines, ldm, s, fp.nbl[st], fp.s[st], tw);
-    else if (r == 5) fft_stage<R, 5, INV>(buf, nlines, ldm, s, fp.nbl[st], fp.s[st], tw);
-    else if (r == 7) fft_stage<R, 7, INV>(buf, nlines, ldm, s, fp.nbl[st], fp.s[st], tw);
+    else if (R57 && r == 5) fft_stage<R, (R57 ? 5 : 2), INV>(buf, nlines, ldm, s, fp.nbl[st], fp.s[st], tw);
+    else if (R57 && r == 7) fft_stage<R, (R57 ? 7 : 2), INV>(buf, nlines, ldm, s, fp.nbl[st], fp.s[st], tw);
     else fft_stage<R, 2, INV>(buf, nlines, ldm, s, fp.nbl[st], fp.s[st], tw);
     s *= r;
   }

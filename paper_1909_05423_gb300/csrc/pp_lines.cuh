@@ -604,8 +604,8 @@ __device__ __noinline__ void post_tile(const LineArgs& a, const cx<R>* buf, int 
 // 512-point lines, which hold 16 values per thread (96).  The run-time-length kernels (radix-3/5/7
 // butterflies) get 64 (FP32) and 128 (double-float).
 template <class R, int MC, bool OY> struct MaxRegs {
-  static constexpr int v = std::is_same<R, float>::value ? (MC == 0 ? 64 : 48)
-                                                         : (MC == 0 ? 128 : ((OY && MC == 512) ? 96 : 64));
+  static constexpr int v = std::is_same<R, float>::value ? (MC <= 0 ? 64 : 48)
+                                                         : (MC <= 0 ? 128 : ((OY && MC == 512) ? 96 : 64));
 };
 
 // One tile per CTA (x: lpc consecutive rows; y: one plane x tx columns).
@@ -613,7 +613,10 @@ template <class R, class SI, class SO, bool OY, int MC>
 __global__ void __maxnreg__((MaxRegs<R, MC, OY>::v)) k_lines(const LineArgs args) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const LineArgs& a = args;
-  const int M = MC ? MC : a.fp.M;
+  // MC > 0: compile-time length; 0: run-time length (radices 2, 3, 4, 8); -1: run-time length
+  // with radix-5/7 stages as well
+  constexpr int MCT = MC > 0 ? MC : 0;
+  const int M = MCT ? MCT : a.fp.M;
   const int ldm = a.ldm;
   cx<R>* buf = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* tws = buf + (size_t)a.lpc * ldm;
@@ -641,7 +644,7 @@ __global__ void __maxnreg__((MaxRegs<R, MC, OY>::v)) k_lines(const LineArgs args
     s_bout[L] = line_base(a, (unsigned)(line0 + L), true);
   }
   __syncthreads();
-  pre_tile<R, OY, MC>(a, SrcGlobal<R, SI>{reinterpret_cast<const SI*>(a.in), s_bin, (long long)a.in_pos}, nl, buf);
+  pre_tile<R, OY, MCT>(a, SrcGlobal<R, SI>{reinterpret_cast<const SI*>(a.in), s_bin, (long long)a.in_pos}, nl, buf);
   __syncthreads();
   if constexpr (MC > 0) {
     // double-float lines of 256+ complex points: radix-8 stages share one copy of the butterfly
@@ -656,11 +659,11 @@ __global__ void __maxnreg__((MaxRegs<R, MC, OY>::v)) k_lines(const LineArgs args
     }
     __syncthreads();  // warp teams synchronised only themselves; post-processing reads every line
   } else {
-    if (inv) fft_lines<R, true>(buf, nl, ldm, a.fp, tws);
-    else fft_lines<R, false>(buf, nl, ldm, a.fp, tws);
+    if (inv) fft_lines<R, true, (MC < 0)>(buf, nl, ldm, a.fp, tws);
+    else fft_lines<R, false, (MC < 0)>(buf, nl, ldm, a.fp, tws);
     if (a.fp.nst == 0) __syncthreads();
   }
-  post_tile<R, SO, OY, MC>(a, buf, nl, s_bout);
+  post_tile<R, SO, OY, MCT>(a, buf, nl, s_bout);
 }
 
 template <class R, class SI, class SO, bool OY, int MC>
@@ -707,8 +710,10 @@ cudaError_t dispatch_io(const LineArgs& a, int oy, int sin, int sout, int thread
 PP_LINES_GROUP_DECL(lines_df_small);
 PP_LINES_GROUP_DECL(lines_df_large);
 PP_LINES_GROUP_DECL(lines_df_any);
+PP_LINES_GROUP_DECL(lines_df_any57);
 PP_LINES_GROUP_DECL(lines_f32_small);
 PP_LINES_GROUP_DECL(lines_f32_large);
 PP_LINES_GROUP_DECL(lines_f32_any);
+PP_LINES_GROUP_DECL(lines_f32_any57);
 
 }  // namespace pp

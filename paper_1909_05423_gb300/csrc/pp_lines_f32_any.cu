@@ -1,4 +1,5 @@
-// pp_lines_f32_any.cu -- FP32 (mixed-precision) line-transform kernels for any FFT length (read at run time).
+// pp_lines_f32_any.cu -- FP32 (mixed-precision) line-transform kernels for run-time FFT lengths with
+// radices 2, 3, 4 and 8.
 #include "pp_lines.cuh"
 
 namespace pp {
