@@ -60,9 +60,9 @@ struct LineArgs {
 constexpr int kMaxLpc = 512;  // lines per CTA (bounded so the per-line bases fit in shared memory)
 constexpr int kHostChunks = 8;  // plane chunks of a host-buffer solve (copies overlap transforms)
 
-// Complex FFT lengths with kernels compiled for the length: powers of two 64..1024.  Their stage
+// Complex FFT lengths with kernels compiled for the length: powers of two 8..1024.  Their stage
 // twiddles are stored per stage in butterfly order (fft_lines_ct); other lengths keep w_M^j, j < M.
-constexpr int kCtMin = 64, kCtMax = 1024;
+constexpr int kCtMin = 8, kCtMax = 1024;
 inline bool ct_length(int M) { return M >= kCtMin && M <= kCtMax && (M & (M - 1)) == 0; }
 
 // Per-mode z-solve descriptor (tables computed on the host in FP64).

@@ -703,14 +703,16 @@ cudaError_t dispatch_io(const LineArgs& a, int oy, int sin, int sout, int thread
 }
 
 // Instantiation groups (one translation unit each, compiled in parallel): compile-time lengths
-// {64, 128, 256} and {512, 1024}, plus the run-time-length kernels.  Each returns
-// cudaErrorNotSupported when the length is not in its group.
+// {8, 16, 32}, {64, 128, 256} and {512, 1024}, plus the run-time-length kernels (without and with
+// radix-5/7 stages).  Each returns cudaErrorNotSupported when the length is not in its group.
 #define PP_LINES_GROUP_DECL(name) \
   cudaError_t name(const LineArgs& a, int oy, int sin, int sout, int threads, cudaStream_t st)
+PP_LINES_GROUP_DECL(lines_df_tiny);
 PP_LINES_GROUP_DECL(lines_df_small);
 PP_LINES_GROUP_DECL(lines_df_large);
 PP_LINES_GROUP_DECL(lines_df_any);
 PP_LINES_GROUP_DECL(lines_df_any57);
+PP_LINES_GROUP_DECL(lines_f32_tiny);
 PP_LINES_GROUP_DECL(lines_f32_small);
 PP_LINES_GROUP_DECL(lines_f32_large);
 PP_LINES_GROUP_DECL(lines_f32_any);

@@ -47,6 +47,20 @@ def test_tiny_all_axis_kinds(oracle, shape):
         assert rel_l2(u, ref) <= TOL_F64, (bc, rel_l2(u, ref))
 
 
+@pytest.mark.parametrize("shape", [(5, 16, 32), (6, 32, 64), (4, 64, 16), (3, 8, 16)])
+@pytest.mark.parametrize("bc", ["NNDDNN", "PPPPDD", "DNNDPP", "PPNDDN", "NNPPND"])
+def test_short_power_of_two_lines(oracle, shape, bc):
+    """FFT lengths 4..32 (kernels compiled for 8, 16, 32; shorter ones at run time), every kind."""
+    nz, ny, nx = shape
+    if bc[4] == "P" and nz < 3:
+        pytest.skip("periodic z needs nz >= 3")
+    sp = (1.0 / nx, 1.0 / ny, 1.0 / nz)
+    f = workloads.uniform_source(shape, seed=sum(shape))
+    ref = oracle.solve(f, bc, sp)
+    for dtype, tol in (("f64", TOL_F64), ("mixed_f64io", 1e-6)):
+        assert rel_l2(gpu_solve(f, bc, sp, dtype), ref) <= tol, dtype
+
+
 def test_config1_manufactured_32(oracle):
     """32^3, periodic x/y, Dirichlet z, u* = sin 2pi x sin 2pi y sin pi z: GPU RMS error equals the
     closed form 1.042987e-03 and the GPU matches the oracle."""
