@@ -57,7 +57,7 @@ struct LineArgs {
   FastDiv fd_nblk;    // column blocks per plane
   FastDiv fd_gpc;     // y: groups of vector-width adjacent lines per CTA
 };
-constexpr int kMaxLpc = 512;  // lines per CTA (bounded so the per-line bases fit in shared memory)
+constexpr int kMaxLpc = 512;  // lines per CTA (bounds the per-line bases in shared memory)
 constexpr int kHostChunks = 8;  // plane chunks of a host-buffer solve (copies overlap transforms)
 
 // Complex FFT lengths with kernels compiled for the length: powers of two 8..1024.  Their stage

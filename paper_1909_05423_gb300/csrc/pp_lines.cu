@@ -5,10 +5,8 @@
 
 namespace pp {
 
-cudaError_t launch_lines_impl(const LineArgs& a, bool df_arith, int oy, int sin, int sout, int threads, size_t smem,
-                              int grid, cudaStream_t st) {
-  (void)smem;
-  (void)grid;
+cudaError_t launch_lines_impl(const LineArgs& a, bool df_arith, int oy, int sin, int sout, int threads,
+                              cudaStream_t st) {
   const int M = a.fp.M;
   const bool tiny = ct_length(M) && M <= 32, small = ct_length(M) && M >= 64 && M <= 256,
              large = ct_length(M) && M >= 512;

@@ -2,14 +2,17 @@
 //
 // A plan fixes the grid, the per-face boundary conditions, the spacings and the arithmetic
 // mode, and precomputes on the host, in FP64:
-//   * the FFT twiddles w_M^j and the pre/post twiddles of the DCT/DST recipes
-//     (angles reduced exactly in integers, then split into double-float pairs);
+//   * the FFT twiddles (w_M^j, or per stage in butterfly order for the compile-time lengths) and
+//     the pre/post twiddles of the DCT/DST recipes (angles reduced exactly in integers, then split
+//     into double-float pairs);
 //   * for every (kx,ky) pair the eigenvalue shift of Table "Eigenvalues"
 //     (lambda = -2 + 2 cos(theta) per axis, divided by h^2, summed over x and y) and the
 //     Thomas multipliers of its z system, evaluated with the same FP64 operations as a
 //     textbook Thomas elimination, truncated once they reach their fixed point.
 // A solve is then five launches on the caller's stream:
 //   x-forward -> y-forward -> z tridiagonal -> y-inverse -> x-inverse.
+// Launch shapes (threads and lines per CTA) are chosen per line kernel and direction, by a
+// heuristic or by timing candidates (autotune()).
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -24,8 +27,10 @@
 #include "pp_internal.h"
 
 namespace pp {
-cudaError_t launch_lines_impl(const LineArgs& a, bool df_arith, int oy, int sin, int sout, int threads, size_t smem,
-                              int grid, cudaStream_t st);
+// the kernel family and instantiation for the launch (pp_lines.cu): double-float or FP32 arithmetic,
+// x (oy = 0) or y (oy = 1) lines, storage codes of input and output
+cudaError_t launch_lines_impl(const LineArgs& a, bool df_arith, int oy, int sin, int sout, int threads,
+                              cudaStream_t st);
 cudaError_t launch_zsolve_impl(const ZArgs& a, bool df_spill, bool zper, cudaStream_t st);
 }  // namespace pp
 
@@ -517,7 +522,7 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
     a.vec_ok = (((uintptr_t)in | (uintptr_t)out) % 32 == 0) ? 1 : 0;
     a.fd_gpc = FastDiv::make(1u);
     finish_args(a);
-    return launch_lines_impl(a, dfm, 0, io_in, io_out, p->threads_x[dir], 0, 0, st);
+    return launch_lines_impl(a, dfm, 0, io_in, io_out, p->threads_x[dir], st);
   }
   // y
   const bool cplx_cols = (p->layout == 0);
@@ -570,7 +575,7 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
   }
   finish_args(a);
   a.fd_nblk = FastDiv::make((unsigned)a.nblk);
-  return launch_lines_impl(a, dfm, 1, io_in, io_out, p->threads_y[dir], 0, 0, st);
+  return launch_lines_impl(a, dfm, 1, io_in, io_out, p->threads_y[dir], st);
 }
 
 cudaError_t launch_zsolve(const pp_plan* p, void* data, int transpose, cudaStream_t st) {
@@ -623,9 +628,9 @@ static pp_status run_pipeline(pp_plan* p, const void* f, void* u, int transpose,
 }
 
 // ------------------------------------------------------------------ autotuner
-// Times candidate launch shapes of the x kernels (x-forward + x-inverse) and of the y kernels
-// (y-forward + y-inverse) on scratch grids and keeps the fastest.  Results are cached per
-// (device, sizes, boundary set, dtype) for the life of the process.
+// Times candidate launch shapes of each of the four line kernels on scratch grids and keeps the
+// fastest.  Results are cached per (device, sizes, boundary set, dtype) for the life of the
+// process.
 namespace {
 struct TuneEnt {
   int dev, nx, ny, nz, dtype, bc[6];
