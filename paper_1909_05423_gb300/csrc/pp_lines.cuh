@@ -21,8 +21,9 @@
 // consecutive threads along a line; y: consecutive threads across columns, so every access is
 // a coalesced row segment), the FFT runs in place in shared memory, post-processing writes
 // global memory in the same patterns.  The kernels are templated on the complex FFT length MC
-// (MC = 0: read from the plan at run time; MC = a power of two: the stage sequence and all
-// index divisions are compile-time).
+// (MC = a power of two 8..1024: the stage sequence and all index divisions are compile-time and
+// each line has its own thread team; MC = 0: the length is read from the plan at run time,
+// radices 2, 3, 4, 8; MC = -1: run-time length with radix-5/7 stages as well).
 #pragma once
 #include <algorithm>
 #include <type_traits>
