@@ -61,7 +61,8 @@ def replica_aggregate(ms_local: float, points_local: int, dist=None, device="cpu
 KERNEL_SOURCES = ("pp_arith.cuh", "pp_fft.cuh", "pp_internal.h", "pp_lines.cuh", "pp_lines.cu", "pp_lines_df_tiny.cu",
                   "pp_lines_f32_tiny.cu", "pp_lines_df_small.cu",
                   "pp_lines_df_large.cu", "pp_lines_df_any.cu", "pp_lines_df_any57.cu", "pp_lines_f32_small.cu",
-                  "pp_lines_f32_large.cu", "pp_lines_f32_any.cu", "pp_lines_f32_any57.cu", "pp_zsolve.cu", "pp_misc.cu")
+                  "pp_lines_f32_large.cu", "pp_lines_f32_any.cu", "pp_lines_f32_any57.cu", "pp_lines_df_ct3a.cu",
+                  "pp_lines_df_ct3b.cu", "pp_lines_f32_ct3a.cu", "pp_lines_f32_ct3b.cu", "pp_zsolve.cu", "pp_misc.cu")
 
 
 def _source_hash():

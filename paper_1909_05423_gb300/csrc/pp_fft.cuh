@@ -63,7 +63,12 @@ constexpr int kCapPerThread = 8;
 // (8 or 16) complex values per thread per stage.  Teams of up to one warp synchronise their stages
 // with the warp alone; wider teams use the CTA barrier.  The y kernels of 512-point lines use
 // VPT = 16 (one warp per line; measured faster), every other kernel VPT = 8.
-constexpr int ct_values_per_thread(int MC, bool y_lines) { return (MC == 512 && y_lines) ? 16 : 8; }
+// Lengths 3 x 2^k (radix-3 last stage) spread the butterflies of all lines over the CTA instead,
+// NBut per thread: at most 6 values (two radix-3 butterflies).
+constexpr bool ct_pow2(int MC) { return (MC & (MC - 1)) == 0; }
+constexpr int ct_values_per_thread(int MC, bool y_lines) {
+  return !ct_pow2(MC) ? 6 : ((MC == 512 && y_lines) ? 16 : 8);
+}
 template <int TPL> __device__ __forceinline__ void team_sync() {
   if constexpr (TPL <= 32) __syncwarp();
   else __syncthreads();
@@ -256,56 +261,98 @@ __device__ __forceinline__ void fft_lines(cx<R>* buf, int nlines, int ldm, const
 }
 
 // ---------------------------------------------------------------- compile-time length
-// For a power-of-two length MC known at compile time the stage sequence (radix 8 while it
-// divides, then 4, then 2) and every index division are resolved by the compiler.
+// For a length MC known at compile time (a power of two, or 3 x 2^k) the stage sequence (radix 8
+// while it divides, then 4, then 2, then 3) and every index division are resolved by the compiler.
 //
 // Addressing: with powers of two, pad(j + u nbl) = pad(j) + u nbl + (u nbl >> 5) and, for the
 // output position o = q + S r p (q < S), pad(o + S t) = pad(o) + S t + (S t >> 5), so every
-// shared-memory access of a butterfly is one base address plus a compile-time offset.
+// shared-memory access of a butterfly is one base address plus a compile-time offset (3 x 2^k
+// lengths compute each padded index).
 // Twiddles are stored per stage in butterfly order: stage k (stride S, radix r, p < MC/(S r))
 // keeps w_MC^(p S t), t = 1..r-1, at off_k + p (r-1) + t-1; off_k = MC - MC/S (the sizes
 // telescope), and the last stage (p = 0, all twiddles 1) keeps none.
-template <int REM> struct CtRadix { static constexpr int v = (REM % 8 == 0) ? 8 : (REM % 4 == 0 ? 4 : 2); };
+template <int REM> struct CtRadix {
+  static constexpr int v = (REM % 8 == 0) ? 8 : (REM % 4 == 0) ? 4 : (REM % 2 == 0) ? 2 : 3;
+};
 
 template <class R, int RAD, bool INV, int MC, int VPT, int S, int TWOFF>
 __device__ __forceinline__ void fft_stage_ct(cx<R>* buf, int nlines, int ldm, const cx<R>* tw) {
   constexpr int nbl = MC / RAD;
-  constexpr int TPL = MC / VPT;
-  constexpr int NB = nbl / TPL;  // butterflies per thread
-  static_assert(NB * TPL == nbl && NB * RAD <= 16, "team covers the line");
-  const int line = (int)threadIdx.x / TPL, lt = (int)threadIdx.x % TPL;
-  const bool act = line < nlines;
-  cx<R> a[NB][RAD];
-  if (act) {
+  if constexpr (!ct_pow2(MC)) {
+    // 3 x 2^k: the butterflies of all lines spread over the CTA, CTA barriers
+    constexpr int NB = NBut<RAD>::v;
+    const int total = nlines * nbl;
+    cx<R> a[NB][RAD];
 #pragma unroll
     for (int i = 0; i < NB; i++) {
-      const cx<R>* x = buf + line * ldm + pad(lt + i * TPL);
+      const int b = threadIdx.x + i * blockDim.x;
+      if (b < total) {
+        const cx<R>* x = buf + (b / nbl) * ldm;
+        const int j = b % nbl;
 #pragma unroll
-      for (int u = 0; u < RAD; u++) a[i][u] = x[u * nbl + ((u * nbl) >> 5)];
-    }
-  }
-  team_sync<TPL>();
-#pragma unroll
-  for (int i = 0; i < NB; i++) {
-    if (act) {
-      const int j = lt + i * TPL;
-      const int p = j / S, q = j % S;
-      dft_r<R, RAD, INV>(a[i]);
-      cx<R>* y = buf + line * ldm + pad(q + S * RAD * p);
-      y[0] = a[i][0];
-      if constexpr (S * RAD == MC) {
-        // last stage: p = 0, every twiddle is 1
-#pragma unroll
-        for (int t = 1; t < RAD; t++) y[S * t + ((S * t) >> 5)] = a[i][t];
-      } else {
-        const cx<R>* w = tw + TWOFF + p * (RAD - 1);  // w[t-1] = w_MC^(p S t)
-#pragma unroll
-        for (int t = 1; t < RAD; t++)
-          y[S * t + ((S * t) >> 5)] = INV ? cmulc(a[i][t], w[t - 1]) : cmul(a[i][t], w[t - 1]);
+        for (int u = 0; u < RAD; u++) a[i][u] = x[pad(j + u * nbl)];
       }
     }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NB; i++) {
+      const int b = threadIdx.x + i * blockDim.x;
+      if (b < total) {
+        const int j = b % nbl;
+        const int p = j / S, q = j % S;
+        dft_r<R, RAD, INV>(a[i]);
+        cx<R>* y = buf + (b / nbl) * ldm;
+        const int o = q + S * RAD * p;
+        y[pad(o)] = a[i][0];
+        if constexpr (S * RAD == MC) {
+#pragma unroll
+          for (int t = 1; t < RAD; t++) y[pad(o + S * t)] = a[i][t];
+        } else {
+          const cx<R>* w = tw + TWOFF + p * (RAD - 1);
+#pragma unroll
+          for (int t = 1; t < RAD; t++) y[pad(o + S * t)] = INV ? cmulc(a[i][t], w[t - 1]) : cmul(a[i][t], w[t - 1]);
+        }
+      }
+    }
+    __syncthreads();
+  } else {
+    constexpr int TPL = MC / VPT;
+    constexpr int NB = nbl / TPL;  // butterflies per thread
+    static_assert(NB * TPL == nbl && NB * RAD <= 16, "team covers the line");
+    const int line = (int)threadIdx.x / TPL, lt = (int)threadIdx.x % TPL;
+    const bool act = line < nlines;
+    cx<R> a[NB][RAD];
+    if (act) {
+#pragma unroll
+      for (int i = 0; i < NB; i++) {
+        const cx<R>* x = buf + line * ldm + pad(lt + i * TPL);
+#pragma unroll
+        for (int u = 0; u < RAD; u++) a[i][u] = x[u * nbl + ((u * nbl) >> 5)];
+      }
+    }
+    team_sync<TPL>();
+#pragma unroll
+    for (int i = 0; i < NB; i++) {
+      if (act) {
+        const int j = lt + i * TPL;
+        const int p = j / S, q = j % S;
+        dft_r<R, RAD, INV>(a[i]);
+        cx<R>* y = buf + line * ldm + pad(q + S * RAD * p);
+        y[0] = a[i][0];
+        if constexpr (S * RAD == MC) {
+          // last stage: p = 0, every twiddle is 1
+#pragma unroll
+          for (int t = 1; t < RAD; t++) y[S * t + ((S * t) >> 5)] = a[i][t];
+        } else {
+          const cx<R>* w = tw + TWOFF + p * (RAD - 1);  // w[t-1] = w_MC^(p S t)
+#pragma unroll
+          for (int t = 1; t < RAD; t++)
+            y[S * t + ((S * t) >> 5)] = INV ? cmulc(a[i][t], w[t - 1]) : cmul(a[i][t], w[t - 1]);
+        }
+      }
+    }
+    team_sync<TPL>();
   }
-  team_sync<TPL>();
 }
 
 // tw: the per-stage table of load_stage_twiddles

@@ -60,10 +60,16 @@ struct LineArgs {
 constexpr int kMaxLpc = 512;  // lines per CTA (bounds the per-line bases in shared memory)
 constexpr int kHostChunks = 8;  // plane chunks of a host-buffer solve (copies overlap transforms)
 
-// Complex FFT lengths with kernels compiled for the length: powers of two 8..1024.  Their stage
-// twiddles are stored per stage in butterfly order (fft_lines_ct); other lengths keep w_M^j, j < M.
+// Complex FFT lengths with kernels compiled for the length: powers of two 8..1024 and 3 x 2^k
+// 24..768.  Their stage twiddles are stored per stage in butterfly order (fft_lines_ct); other
+// lengths keep w_M^j, j < M.
 constexpr int kCtMin = 8, kCtMax = 1024;
-inline bool ct_length(int M) { return M >= kCtMin && M <= kCtMax && (M & (M - 1)) == 0; }
+inline bool ct_length(int M) {
+  const bool p2 = M >= kCtMin && M <= kCtMax && (M & (M - 1)) == 0;
+  const int t = M / 3;
+  const bool p3 = M % 3 == 0 && t >= 8 && t <= 256 && (t & (t - 1)) == 0;
+  return p2 || p3;
+}
 
 // Per-mode z-solve descriptor (tables computed on the host in FP64).
 struct ZMode {

@@ -21,8 +21,8 @@
 // consecutive threads along a line; y: consecutive threads across columns, so every access is
 // a coalesced row segment), the FFT runs in place in shared memory, post-processing writes
 // global memory in the same patterns.  The kernels are templated on the complex FFT length MC
-// (MC = a power of two 8..1024: the stage sequence and all index divisions are compile-time and
-// each line has its own thread team; MC = 0: the length is read from the plan at run time,
+// (MC = a power of two 8..1024, or 3 x 2^k 24..768: the stage sequence and all index divisions
+// are compile-time, and for powers of two each line has its own thread team; MC = 0: the length is read from the plan at run time,
 // radices 2, 3, 4, 8; MC = -1: run-time length with radix-5/7 stages as well).
 #pragma once
 #include <algorithm>
@@ -600,13 +600,14 @@ __device__ __noinline__ void post_tile(const LineArgs& a, const cx<R>* buf, int 
   }
 }
 
-// Register caps (measured; none of these spills in the compile-time-length kernels): FP32 48
-// (ten 128-thread CTAs per SM); double-float 64 (eight), except the warp-per-line y kernels of
-// 512-point lines, which hold 16 values per thread (96).  The run-time-length kernels (radix-3/5/7
-// butterflies) get 64 (FP32) and 128 (double-float).
+// Register caps (measured; none of these spills in the compile-time-length kernels): FP32 48 (ten
+// 128-thread CTAs per SM); double-float 64 (eight), except the warp-per-line y kernels of
+// 512-point lines, which hold 16 values per thread (96).  The run-time-length kernels get 64
+// (FP32) and 128 (double-float).
 template <class R, int MC, bool OY> struct MaxRegs {
-  static constexpr int v = std::is_same<R, float>::value ? (MC <= 0 ? 64 : 48)
-                                                         : (MC <= 0 ? 128 : ((OY && MC == 512) ? 96 : 64));
+  static constexpr bool RT = MC <= 0;  // run-time lengths
+  static constexpr int v = std::is_same<R, float>::value ? (RT ? 64 : 48)
+                                                         : (RT ? 128 : ((OY && MC == 512) ? 96 : 64));
 };
 
 // One tile per CTA (x: lpc consecutive rows; y: one plane x tx columns).
@@ -651,7 +652,7 @@ __global__ void __maxnreg__((MaxRegs<R, MC, OY>::v)) k_lines(const LineArgs args
     // double-float lines of 256+ complex points: radix-8 stages share one copy of the butterfly
     // (measured faster there; the shorter lengths keep fully compile-time stages)
     constexpr int VPT = ct_values_per_thread(MC, OY);
-    if constexpr (std::is_same<R, df>::value && MC >= 256) {
+    if constexpr (std::is_same<R, df>::value && MC >= 256 && ct_pow2(MC)) {
       if (inv) fft_lines_lp<R, true, MC, VPT>(buf, nl, ldm, tws);
       else fft_lines_lp<R, false, MC, VPT>(buf, nl, ldm, tws);
     } else {
@@ -704,18 +705,22 @@ cudaError_t dispatch_io(const LineArgs& a, int oy, int sin, int sout, int thread
 }
 
 // Instantiation groups (one translation unit each, compiled in parallel): compile-time lengths
-// {8, 16, 32}, {64, 128, 256} and {512, 1024}, plus the run-time-length kernels (without and with
-// radix-5/7 stages).  Each returns cudaErrorNotSupported when the length is not in its group.
+// {8, 16, 32}, {64, 128, 256}, {512, 1024}, {24, 48, 96} and {192, 384, 768}, plus the
+// run-time-length kernels (without and with radix-5/7 stages).  Each returns cudaErrorNotSupported when the length is not in its group.
 #define PP_LINES_GROUP_DECL(name) \
   cudaError_t name(const LineArgs& a, int oy, int sin, int sout, int threads, cudaStream_t st)
 PP_LINES_GROUP_DECL(lines_df_tiny);
 PP_LINES_GROUP_DECL(lines_df_small);
 PP_LINES_GROUP_DECL(lines_df_large);
+PP_LINES_GROUP_DECL(lines_df_ct3a);
+PP_LINES_GROUP_DECL(lines_df_ct3b);
 PP_LINES_GROUP_DECL(lines_df_any);
 PP_LINES_GROUP_DECL(lines_df_any57);
 PP_LINES_GROUP_DECL(lines_f32_tiny);
 PP_LINES_GROUP_DECL(lines_f32_small);
 PP_LINES_GROUP_DECL(lines_f32_large);
+PP_LINES_GROUP_DECL(lines_f32_ct3a);
+PP_LINES_GROUP_DECL(lines_f32_ct3b);
 PP_LINES_GROUP_DECL(lines_f32_any);
 PP_LINES_GROUP_DECL(lines_f32_any57);
 

@@ -1,0 +1,13 @@
+// pp_lines_df_ct3b.cu -- double-float (FP64-class) line-transform kernels for FFT lengths 192, 384, 768.
+#include "pp_lines.cuh"
+
+namespace pp {
+PP_LINES_GROUP_DECL(lines_df_ct3b) {
+  switch (a.fp.M) {
+    case 192: return dispatch_io<df, float2, 192>(a, oy, sin, sout, threads, st);
+    case 384: return dispatch_io<df, float2, 384>(a, oy, sin, sout, threads, st);
+    case 768: return dispatch_io<df, float2, 768>(a, oy, sin, sout, threads, st);
+    default: return cudaErrorNotSupported;
+  }
+}
+}  // namespace pp

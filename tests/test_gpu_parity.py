@@ -61,6 +61,18 @@ def test_short_power_of_two_lines(oracle, shape, bc):
         assert rel_l2(gpu_solve(f, bc, sp, dtype), ref) <= tol, dtype
 
 
+@pytest.mark.parametrize("shape", [(5, 48, 96), (4, 96, 48), (3, 192, 384), (3, 768, 24), (4, 36, 1536)])
+@pytest.mark.parametrize("bc", ["NNDDNN", "PPPPDD", "DNNDPP", "PPNDDN"])
+def test_three_times_power_of_two_lines(oracle, shape, bc):
+    """FFT lengths 3 x 2^k (kernels compiled for 24..768, radix-3 last stage), every kind."""
+    nz, ny, nx = shape
+    sp = (1.0 / nx, 1.0 / ny, 1.0 / nz)
+    f = workloads.uniform_source(shape, seed=sum(shape) + 1)
+    ref = oracle.solve(f, bc, sp)
+    for dtype, tol in (("f64", TOL_F64), ("mixed_f64io", 1e-6)):
+        assert rel_l2(gpu_solve(f, bc, sp, dtype), ref) <= tol, dtype
+
+
 def test_config1_manufactured_32(oracle):
     """32^3, periodic x/y, Dirichlet z, u* = sin 2pi x sin 2pi y sin pi z: GPU RMS error equals the
     closed form 1.042987e-03 and the GPU matches the oracle."""
