@@ -61,13 +61,13 @@ constexpr int kCapPerThread = 8;
 
 // Compile-time lengths transform every line with its own team of MC/VPT consecutive threads, VPT
 // (8 or 16) complex values per thread per stage.  Teams of up to one warp synchronise their stages
-// with the warp alone; wider teams use the CTA barrier.  The y kernels of 512-point lines use
-// VPT = 16 (one warp per line; measured faster), every other kernel VPT = 8.
+// with the warp alone; wider teams use the CTA barrier.  The 512-point y kernels, and the FP32 x
+// kernels of that length, use VPT = 16 (one warp per line; measured faster), the others VPT = 8.
 // Lengths 3 x 2^k (radix-3 last stage) spread the butterflies of all lines over the CTA instead,
 // NBut per thread: at most 6 values (two radix-3 butterflies).
 constexpr bool ct_pow2(int MC) { return (MC & (MC - 1)) == 0; }
-constexpr int ct_values_per_thread(int MC, bool y_lines) {
-  return !ct_pow2(MC) ? 6 : ((MC == 512 && y_lines) ? 16 : 8);
+constexpr int ct_values_per_thread(int MC, bool y_lines, bool df_arith) {
+  return !ct_pow2(MC) ? 6 : ((MC == 512 && (y_lines || !df_arith)) ? 16 : 8);
 }
 template <int TPL> __device__ __forceinline__ void team_sync() {
   if constexpr (TPL <= 32) __syncwarp();

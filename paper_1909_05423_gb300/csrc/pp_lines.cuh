@@ -652,7 +652,7 @@ __global__ void __maxnreg__((MaxRegs<R, MC, OY>::v)) k_lines(const LineArgs args
   if constexpr (MC > 0) {
     // double-float lines of 256+ complex points: radix-8 stages share one copy of the butterfly
     // (measured faster there; the shorter lengths keep fully compile-time stages)
-    constexpr int VPT = ct_values_per_thread(MC, OY);
+    constexpr int VPT = ct_values_per_thread(MC, OY, std::is_same<R, df>::value);
     if constexpr (std::is_same<R, df>::value && MC >= 256 && ct_pow2(MC)) {
       if (inv) fft_lines_lp<R, true, MC, VPT>(buf, nl, ldm, tws);
       else fft_lines_lp<R, false, MC, VPT>(buf, nl, ldm, tws);

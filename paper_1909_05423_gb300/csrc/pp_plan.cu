@@ -372,11 +372,12 @@ static void free_plan(pp_plan* p) {
   delete p;
 }
 
-// Complex values a thread holds per FFT stage: 16 in the y kernels of 512-point lines (one warp per
-// line), 8 in the other compile-time-length kernels, and for run-time lengths the smallest stage
-// capacity of the line's radices: lines per CTA x M must not exceed this x threads.
-static int values_per_thread(const FftPlan& fp, int axis) {
-  if (ct_length(fp.M)) return ct_values_per_thread(fp.M, axis == 1);
+// Complex values a thread holds per FFT stage: 16 in the y kernels of 512-point lines and the FP32
+// x kernels of that length (one warp per line), 8 in the other power-of-two kernels, 6 for
+// 3 x 2^k, and for run-time lengths the smallest stage capacity of the line's radices: lines per
+// CTA x M must not exceed this x threads.
+static int values_per_thread(const FftPlan& fp, int axis, bool df_arith) {
+  if (ct_length(fp.M)) return ct_values_per_thread(fp.M, axis == 1, df_arith);
   int c = kCapPerThread;
   for (int i = 0; i < fp.nst; i++) c = std::min(c, stage_capacity(fp.rad[i]));
   return c;
@@ -403,7 +404,7 @@ static void choose_shapes(pp_plan* p, const pp_plan_options* opt) {
     {
       int M = p->fx.M;
       // a CTA must hold at least one whole line: threads * (values per thread) >= M
-      const int cpt = values_per_thread(p->fx, 0);
+      const int cpt = values_per_thread(p->fx, 0, p->dtype == PP_F64);
       const int tmin = std::max(32, ((M + cpt - 1) / cpt + 31) / 32 * 32);
       int T = tx_req ? tx_req : 128;
       T = std::max(T, tmin);
@@ -428,7 +429,7 @@ static void choose_shapes(pp_plan* p, const pp_plan_options* opt) {
       int ncols = cplx_cols ? p->nx / 2 + 1 : p->nx;
       size_t col_bytes = (cplx_cols ? 2 : 1) * se;
       // CTA size: 128 threads unless that leaves column segments below one 32-byte sector
-      const int cpt = values_per_thread(p->fy, 1);
+      const int cpt = values_per_thread(p->fy, 1, p->dtype == PP_F64);
       const int tmin = std::max(32, ((M + cpt - 1) / cpt + 31) / 32 * 32);
       int T = 128;
       const int tmax = 512;
@@ -516,7 +517,7 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
     out = static_cast<char*>(out) + (size_t)z0 * a.out_plane * st_bytes(p, io_out);
     a.in = in;
     a.out = out;
-    if ((long long)a.lpc * a.fp.M > (long long)values_per_thread(a.fp, 0) * p->threads_x[dir])
+    if ((long long)a.lpc * a.fp.M > (long long)values_per_thread(a.fp, 0, dfm) * p->threads_x[dir])
       return cudaErrorInvalidConfiguration;
     a.ntiles = (a.nlines + a.lpc - 1) / a.lpc;
     a.vec_ok = (((uintptr_t)in | (uintptr_t)out) % 32 == 0) ? 1 : 0;
@@ -556,7 +557,7 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
   out = static_cast<char*>(out) + (size_t)z0 * a.out_plane * st_bytes(p, io_out);
   a.in = in;
   a.out = out;
-  if ((long long)a.lpc * a.fp.M > (long long)values_per_thread(a.fp, 1) * p->threads_y[dir])
+  if ((long long)a.lpc * a.fp.M > (long long)values_per_thread(a.fp, 1, dfm) * p->threads_y[dir])
     return cudaErrorInvalidConfiguration;
   a.tx = a.lpc / parts;
   a.ncols = ncols;
