@@ -91,12 +91,13 @@ def _traffic(stage: str, n: int):
 
 # ---------------------------------------------------------------- ALU roofline of the line kernels
 # FP32 operations of the algorithm, counted as issued FP32 lane instructions (an FMA is one):
-# double-float add 11 (TwoSum 6, two lo adds, FastTwoSum 3), multiply 7 (FMUL, 3 FFMA, FastTwoSum),
-# complex multiply 38 (two fused a*b -+ c*d of 19), complex add 22, halving 2; FP32: add 1, multiply 1,
+# double-float in the unnormalised forms the line kernels use: add 8 (TwoSum 6, two lo adds),
+# multiply 4 (FMUL, 3 FFMA), complex multiply 32 (two fused a*b -+ c*d of 16: two TwoProds 4,
+# TwoSum 6, 6 adds and FMAs of the error terms), complex add 16, halving 2; FP32: add 1, multiply 1,
 # complex multiply 4, complex add 2.  Peak: 152 SMs x 128 FP32 lanes x 2.07 GHz (maximum SM clock).
 FP32_LANES = 152 * 128
 SM_MAX_GHZ = 2.07
-_OPS = {"df": {"add": 11, "mul": 7, "cmul": 38, "half": 2}, "f32": {"add": 1, "mul": 1, "cmul": 4, "half": 1}}
+_OPS = {"df": {"add": 8, "mul": 4, "cmul": 32, "half": 2}, "f32": {"add": 1, "mul": 1, "cmul": 4, "half": 1}}
 
 
 def fft_ops(M: int, arith: str) -> float:

@@ -75,6 +75,41 @@ __device__ __forceinline__ df dot2_sub(df a, df b, df c, df d) {
 __device__ __forceinline__ df dot2_add(df a, df b, df c, df d) { return dot2_sub(a, b, -c, d); }
 __device__ __forceinline__ df df_half(df a) { return df{0.5f * a.hi, 0.5f * a.lo}; }
 
+// Unnormalised forms for the line transforms.  The leading parts are still summed (TwoSum) or
+// multiplied (TwoProd) exactly and the trailing part still collects every error term, but the
+// final FastTwoSum that makes |lo| <= ulp(hi)/2 is skipped (3 of 11 instructions of a sum, 3 of
+// 7 of a product).  hi + lo keeps its value; lo only grows by about ulp(hi) per operation, so
+// after the ~15 operations a transform applies to a value the rounding error of lo stays near
+// 2^-48 of the magnitudes the value was computed from, the norm-wise accuracy of the FFT.
+// Products and sums read unnormalised pairs correctly: TwoSum and TwoProd need no ordering of
+// their operands, and lo enters only through FP32 adds and FMAs.
+__device__ __forceinline__ df add_u(df a, df b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  return df{s, __fadd_rn(e, __fadd_rn(a.lo, b.lo))};
+}
+__device__ __forceinline__ df mul_u(df a, df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df{p, e};
+}
+__device__ __forceinline__ df dot2_sub_u(df a, df b, df c, df d) {
+  const float p1 = __fmul_rn(a.hi, b.hi);
+  const float e1 = __fmaf_rn(a.hi, b.hi, -p1);
+  const float p2 = __fmul_rn(c.hi, d.hi);
+  const float e2 = __fmaf_rn(c.hi, d.hi, -p2);
+  float s, e;
+  two_sum(p1, -p2, s, e);
+  e = __fadd_rn(e, __fsub_rn(e1, e2));
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  e = __fmaf_rn(-c.hi, d.lo, e);
+  e = __fmaf_rn(-c.lo, d.hi, e);
+  return df{s, e};
+}
+
 // df reciprocal: one Newton step on the FP32 reciprocal.
 __device__ __forceinline__ df df_rcp(df a) {
   float r = __frcp_rn(a.hi);
@@ -197,10 +232,12 @@ template <> struct Ar<float> {
   __device__ static __forceinline__ float dsub(float a, float b, float c, float d) { return fmaf(a, b, -c * d); }
   __device__ static __forceinline__ float dadd(float a, float b, float c, float d) { return fmaf(a, b, c * d); }
 };
+// The line transforms compute with the unnormalised forms (above); the z solve's recurrences
+// use the normalised operators.
 template <> struct Ar<df> {
-  __device__ static __forceinline__ df add(df a, df b) { return a + b; }
-  __device__ static __forceinline__ df sub(df a, df b) { return a - b; }
-  __device__ static __forceinline__ df mul(df a, df b) { return a * b; }
+  __device__ static __forceinline__ df add(df a, df b) { return add_u(a, b); }
+  __device__ static __forceinline__ df sub(df a, df b) { return add_u(a, -b); }
+  __device__ static __forceinline__ df mul(df a, df b) { return mul_u(a, b); }
   __device__ static __forceinline__ df neg(df a) { return -a; }
   __device__ static __forceinline__ df half(df a) { return df_half(a); }
   __device__ static __forceinline__ df zero() { return df{0.0f, 0.0f}; }
@@ -208,8 +245,8 @@ template <> struct Ar<df> {
   __device__ static __forceinline__ df sqrt1_2() { return df{0x1.6a09e6p-1f, 0x1.9fcef4p-27f}; }
   __device__ static __forceinline__ df sqrt3_2() { return df{0x1.bb67aep-1f, 0x1.0b0996p-26f}; }
   __device__ static __forceinline__ df sqrt2() { return df{0x1.6a09e6p+0f, 0x1.9fcef4p-26f}; }
-  __device__ static __forceinline__ df dsub(df a, df b, df c, df d) { return dot2_sub(a, b, c, d); }
-  __device__ static __forceinline__ df dadd(df a, df b, df c, df d) { return dot2_add(a, b, c, d); }
+  __device__ static __forceinline__ df dsub(df a, df b, df c, df d) { return dot2_sub_u(a, b, c, d); }
+  __device__ static __forceinline__ df dadd(df a, df b, df c, df d) { return dot2_sub_u(a, b, -c, d); }
 };
 
 // ------------------------------------------------------------------ complex
