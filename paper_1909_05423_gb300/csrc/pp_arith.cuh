@@ -278,23 +278,34 @@ template <class R> __device__ __forceinline__ cx<R> cscale(cx<R> a, R s) { retur
 // --------------------------------------------------------- storage <-> R
 // Storage kinds: IO_F64 (double), IO_F32 (float), SP_DF (float2 hi/lo pair), SP_F32 (float).
 template <class R, class S> struct Io;
+// ld = cv(raw): raw() issues the load, cv() converts its bits.
 template <> struct Io<df, double> {
+  __device__ static __forceinline__ double raw(const double* p, long long i) { return __ldg(p + i); }
+  __device__ static __forceinline__ df cv(double v) { return df_from_double(v); }
   __device__ static __forceinline__ df ld(const double* p, long long i) { return df_from_double(__ldg(p + i)); }
   __device__ static __forceinline__ void st(double* p, long long i, df v) { p[i] = df_to_double(v); }
 };
 template <> struct Io<df, float2> {
+  __device__ static __forceinline__ float2 raw(const float2* p, long long i) { return __ldg(p + i); }
+  __device__ static __forceinline__ df cv(float2 v) { return df{v.x, v.y}; }
   __device__ static __forceinline__ df ld(const float2* p, long long i) { float2 v = p[i]; return df{v.x, v.y}; }
   __device__ static __forceinline__ void st(float2* p, long long i, df v) { p[i] = make_float2(v.hi, v.lo); }
 };
 template <> struct Io<df, float> {
+  __device__ static __forceinline__ float raw(const float* p, long long i) { return __ldg(p + i); }
+  __device__ static __forceinline__ df cv(float v) { return df{v, 0.0f}; }
   __device__ static __forceinline__ df ld(const float* p, long long i) { return df{p[i], 0.0f}; }
   __device__ static __forceinline__ void st(float* p, long long i, df v) { p[i] = df_to_f32(v); }
 };
 template <> struct Io<float, double> {
+  __device__ static __forceinline__ double raw(const double* p, long long i) { return __ldg(p + i); }
+  __device__ static __forceinline__ float cv(double v) { return f32_from_double(v); }
   __device__ static __forceinline__ float ld(const double* p, long long i) { return f32_from_double(__ldg(p + i)); }
   __device__ static __forceinline__ void st(double* p, long long i, float v) { p[i] = double_from_f32(v); }
 };
 template <> struct Io<float, float> {
+  __device__ static __forceinline__ float raw(const float* p, long long i) { return __ldg(p + i); }
+  __device__ static __forceinline__ float cv(float v) { return v; }
   __device__ static __forceinline__ float ld(const float* p, long long i) { return p[i]; }
   __device__ static __forceinline__ void st(float* p, long long i, float v) { p[i] = v; }
 };

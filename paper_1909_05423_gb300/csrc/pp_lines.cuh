@@ -32,6 +32,21 @@
 
 namespace pp {
 
+// cp.async copy of one complex value from global to shared memory (16 bytes: bypasses L1;
+// 8 bytes: through L1), and the commit / wait of this thread's copies.
+template <class R> __device__ __forceinline__ void cp_async_cx(cx<R>* s, const cx<R>* g) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
+  const size_t ga = __cvta_generic_to_global(g);
+  if constexpr (sizeof(cx<R>) == 16) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(ga) : "memory");
+  } else {
+    static_assert(sizeof(cx<R>) == 8, "complex value of 8 or 16 bytes");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(ga) : "memory");
+  }
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // base offsets (in reals) of global line g of the launch
 __device__ __forceinline__ long long line_base(const LineArgs& a, unsigned g, bool out) {
   unsigned plane = a.fd_lpp.div(g);
@@ -71,39 +86,49 @@ __device__ __forceinline__ void for_items(const LineArgs& a, int nl, const FastD
 
 // Vector access to 2 or 4 consecutive reals at a real offset that is a multiple of 2 / 4
 // (rows of x tiles are 16-byte aligned; the host checks the array pointers).
+// raw(): the loaded bits, cvt(): their conversion to R (split so that a batch of loads can be
+// issued before the first conversion waits for its data).
 template <class R, class S> struct Vec;
 template <> struct Vec<df, double> {
-  __device__ static __forceinline__ void ld2(const double* p, long long o, df* v) {
-    double2 a = __ldg(reinterpret_cast<const double2*>(p + o));
-    v[0] = df_from_double(a.x); v[1] = df_from_double(a.y);
+  using raw_t = double2;
+  __device__ static __forceinline__ raw_t raw(const double* p, long long o) {
+    return __ldg(reinterpret_cast<const double2*>(p + o));
   }
+  __device__ static __forceinline__ void cvt(raw_t a, df* v) { v[0] = df_from_double(a.x); v[1] = df_from_double(a.y); }
+  __device__ static __forceinline__ void ld2(const double* p, long long o, df* v) { cvt(raw(p, o), v); }
   __device__ static __forceinline__ void st2(double* p, long long o, const df* v) {
     *reinterpret_cast<double2*>(p + o) = make_double2(df_to_double(v[0]), df_to_double(v[1]));
   }
 };
 template <> struct Vec<df, float2> {
-  __device__ static __forceinline__ void ld2(const float2* p, long long o, df* v) {
-    float4 a = __ldg(reinterpret_cast<const float4*>(p + o));
-    v[0] = df{a.x, a.y}; v[1] = df{a.z, a.w};
+  using raw_t = float4;
+  __device__ static __forceinline__ raw_t raw(const float2* p, long long o) {
+    return __ldg(reinterpret_cast<const float4*>(p + o));
   }
+  __device__ static __forceinline__ void cvt(raw_t a, df* v) { v[0] = df{a.x, a.y}; v[1] = df{a.z, a.w}; }
+  __device__ static __forceinline__ void ld2(const float2* p, long long o, df* v) { cvt(raw(p, o), v); }
   __device__ static __forceinline__ void st2(float2* p, long long o, const df* v) {
     *reinterpret_cast<float4*>(p + o) = make_float4(v[0].hi, v[0].lo, v[1].hi, v[1].lo);
   }
 };
 template <> struct Vec<float, double> {
-  __device__ static __forceinline__ void ld2(const double* p, long long o, float* v) {
-    double2 a = __ldg(reinterpret_cast<const double2*>(p + o));
-    v[0] = f32_from_double(a.x); v[1] = f32_from_double(a.y);
+  using raw_t = double2;
+  __device__ static __forceinline__ raw_t raw(const double* p, long long o) {
+    return __ldg(reinterpret_cast<const double2*>(p + o));
   }
+  __device__ static __forceinline__ void cvt(raw_t a, float* v) { v[0] = f32_from_double(a.x); v[1] = f32_from_double(a.y); }
+  __device__ static __forceinline__ void ld2(const double* p, long long o, float* v) { cvt(raw(p, o), v); }
   __device__ static __forceinline__ void st2(double* p, long long o, const float* v) {
     *reinterpret_cast<double2*>(p + o) = make_double2(double_from_f32(v[0]), double_from_f32(v[1]));
   }
 };
 template <> struct Vec<float, float> {
-  __device__ static __forceinline__ void ld2(const float* p, long long o, float* v) {
-    float2 a = __ldg(reinterpret_cast<const float2*>(p + o));
-    v[0] = a.x; v[1] = a.y;
+  using raw_t = float2;
+  __device__ static __forceinline__ raw_t raw(const float* p, long long o) {
+    return __ldg(reinterpret_cast<const float2*>(p + o));
   }
+  __device__ static __forceinline__ void cvt(raw_t a, float* v) { v[0] = a.x; v[1] = a.y; }
+  __device__ static __forceinline__ void ld2(const float* p, long long o, float* v) { cvt(raw(p, o), v); }
   __device__ static __forceinline__ void st2(float* p, long long o, const float* v) {
     *reinterpret_cast<float2*>(p + o) = make_float2(v[0], v[1]);
   }
@@ -163,6 +188,35 @@ __device__ __forceinline__ void for_groups(const LineArgs& a, int nl, const Fast
   }
 }
 
+// Batched form of for_items for x tiles of a compile-time length: a thread first issues the loads
+// of U items (ld returns their raw bits), then converts and stores them (st), so U items' global
+// loads are in flight together; a plain loop waits for each load before the shared-memory store
+// that the next load cannot pass.  (Measured: x kernels 4-11% faster; the y tiles' 16-byte loads
+// gained nothing, and the FP32 y kernels lost occupancy to the extra registers.)
+// Batch size: `full` items for the compile-time power-of-two lengths from 256 on, half of it
+// elsewhere (their kernels have fewer registers to spare under the caps; the FP32 kernels' 48
+// take half as well).
+constexpr int pre_batch(int MC, int full) { return (MC >= 256 && (MC & (MC - 1)) == 0) ? full : (full > 1 ? full / 2 : 1); }
+
+template <int KC, int U, class LD, class ST>
+__device__ __forceinline__ void for_items_xb(int nl, LD&& ld, ST&& st) {
+  const int tot = nl * KC;
+  for (int t0 = threadIdx.x; t0 < tot; t0 += U * (int)blockDim.x) {
+    decltype(ld(0, 0)) r[U];
+    int L[U], k[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int t = t0 + u * (int)blockDim.x;
+      L[u] = t < tot ? t / KC : -1;
+      k[u] = t % KC;
+      if (L[u] >= 0) r[u] = ld(L[u], k[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++)
+      if (L[u] >= 0) st(L[u], k[u], r[u]);
+  }
+}
+
 template <class R, class SI> struct SrcGlobal {
   using elem_t = SI;
   const SI* in;
@@ -189,14 +243,21 @@ __device__ __noinline__ void pre_tile(const LineArgs& a, const Src src, int nl, 
       if (kind == LK_DCT2 || kind == LK_DST2) {
         // u[4k..4k+3] -> z_k = (u_4k, u_4k+2), z_{M-1-k} = (u_4k+3, u_4k+1) (negated for DST-II)
         const bool dst = (kind == LK_DST2);
-        for_items<false, MC / 2>(a, nl, fk, [&](int L, int k) {
-          const long long b = src.base(L) + 4LL * k;
-          R v[4];
-          Vec<R, SI>::ld2(src.in, b, v);
-          Vec<R, SI>::ld2(src.in, b + 2, v + 2);
-          buf[L * ldm + pad(k)] = cx<R>{v[0], v[2]};
-          buf[L * ldm + pad((M - 1 - k))] = dst ? cx<R>{Ar<R>::neg(v[3]), Ar<R>::neg(v[1])} : cx<R>{v[3], v[1]};
-        });
+        using raw_t = typename Vec<R, SI>::raw_t;
+        struct Raw { raw_t a, b; };
+        for_items_xb<MC / 2, pre_batch(MC, std::is_same<R, df>::value ? 4 : 2)>(
+            nl,
+            [&](int L, int k) {
+              const long long b = src.base(L) + 4LL * k;
+              return Raw{Vec<R, SI>::raw(src.in, b), Vec<R, SI>::raw(src.in, b + 2)};
+            },
+            [&](int L, int k, const Raw& r) {
+              R v[4];
+              Vec<R, SI>::cvt(r.a, v);
+              Vec<R, SI>::cvt(r.b, v + 2);
+              buf[L * ldm + pad(k)] = cx<R>{v[0], v[2]};
+              buf[L * ldm + pad((M - 1 - k))] = dst ? cx<R>{Ar<R>::neg(v[3]), Ar<R>::neg(v[1])} : cx<R>{v[3], v[1]};
+            });
         return;
       }
       if (kind == LK_DCT4 || kind == LK_DST4) {
@@ -222,6 +283,37 @@ __device__ __noinline__ void pre_tile(const LineArgs& a, const Src src, int nl, 
         });
         return;
       }
+    }
+    if (kind == LK_DCT3 || kind == LK_DST3) {
+      // as the Hermitian-pair path below, with the four loads of two items issued together
+      const cx<R>* w4 = aux + (M + 1);
+      const bool c3 = (kind == LK_DCT3);
+      struct Raw { SI y0, y1, y2, y3; };  // Y_k, Y_{N-k} (Y_N = 0), Y_{M-k}, Y_{M+k}
+      for_items_xb<MC / 2 + 1, pre_batch(MC, 2)>(
+          nl,
+          [&](int L, int k) {
+            const long long b = src.base(L);
+            auto row = [&](int j) -> long long { return (long long)(c3 ? j : N - 1 - j) * src.pos; };
+            Raw r;
+            r.y0 = Io<R, SI>::raw(src.in, b + row(k));
+            r.y1 = Io<R, SI>::raw(src.in, b + row(k > 0 ? N - k : 0));
+            r.y2 = Io<R, SI>::raw(src.in, b + row(M - k));
+            r.y3 = Io<R, SI>::raw(src.in, b + row(M + k));
+            return r;
+          },
+          [&](int L, int k, const Raw& r) {
+            const R y1 = k > 0 ? Io<R, SI>::cv(r.y1) : Ar<R>::zero();
+            cx<R> Xk = cmulc(cx<R>{Io<R, SI>::cv(r.y0), Ar<R>::neg(y1)}, w4[k]);
+            cx<R> Xm = cmulc(cx<R>{Io<R, SI>::cv(r.y2), Ar<R>::neg(Io<R, SI>::cv(r.y3))}, w4[M - k]);
+            if (k == 0) { Xk.im = Ar<R>::zero(); Xm.im = Ar<R>::zero(); }
+            cx<R> Xc = cconj(Xm);
+            cx<R> E = cadd(Xk, Xc);
+            cx<R> O = cmulc(csub(Xk, Xc), aux[k]);  // * conj(w_N^k)
+            buf[L * ldm + pad(k)] = cx<R>{Ar<R>::sub(E.re, O.im), Ar<R>::add(E.im, O.re)};
+            const int km = M - k;
+            if (k > 0 && km != k) buf[L * ldm + pad(km)] = cx<R>{Ar<R>::add(E.re, O.im), Ar<R>::sub(O.re, E.im)};
+          });
+      return;
     }
   }
   if constexpr (OY) {
@@ -627,8 +719,11 @@ __global__ void __maxnreg__((MaxRegs<R, MC, OY>::v)) k_lines(const LineArgs args
   long long* s_bin = reinterpret_cast<long long*>(tws + M);
   long long* s_bout = s_bin + a.lpc;
   const cx<R>* twg = reinterpret_cast<const cx<R>*>(a.tw);
-  // stage twiddles: w_M^j, j < M (run-time lengths) or the per-stage table of fft_lines_ct
-  for (int i = threadIdx.x; i < M; i += blockDim.x) tws[i] = twg[i];
+  // stage twiddles: w_M^j, j < M (run-time lengths) or the per-stage table of fft_lines_ct.
+  // Asynchronous copies (cp.async), waited for after the pre-processing: their latency then
+  // overlaps the line loads instead of preceding them.
+  for (int i = threadIdx.x; i < M; i += blockDim.x) cp_async_cx(tws + i, twg + i);
+  cp_async_commit();
   const int kind = a.kind;
   const bool inv = (kind == LK_C2R || kind == LK_C2C_I || kind == LK_DCT3 || kind == LK_DST3);
   int line0, nl;
@@ -648,6 +743,7 @@ __global__ void __maxnreg__((MaxRegs<R, MC, OY>::v)) k_lines(const LineArgs args
   }
   __syncthreads();
   pre_tile<R, OY, MCT>(a, SrcGlobal<R, SI>{reinterpret_cast<const SI*>(a.in), s_bin, (long long)a.in_pos}, nl, buf);
+  cp_async_wait_all();
   __syncthreads();
   if constexpr (MC > 0) {
     // double-float lines of 256+ complex points: radix-8 stages share one copy of the butterfly
