@@ -81,8 +81,17 @@ __device__ __noinline__ void z_singular(S* base, long long P, int n, df scale, c
 }
 
 // MODE 0: Thomas; 1: periodic z (Sherman-Morrison); 2: transposed factorisation (adjoint).
+// Batches wholly inside the converged part of the multipliers (and past the q prefix, before the
+// last row) skip the per-row tests.  That is worth its extra registers where the sweeps are bound
+// by instruction issue, the FP32 spill and the cyclic double-float sweeps (measured), and not in
+// the Thomas double-float sweeps, which run at the copy bandwidth without it.
+template <class S, int MODE> struct ZFast { static constexpr bool v = sizeof(S) == 4 || MODE == 1; };
+// CTAs of 256 threads per SM the register allocation must allow: 4 (64 registers) for the
+// Thomas double-float sweeps, 3 (85) where the batches have a fast path.
+template <class S, int MODE> struct ZMinBlocks { static constexpr int v = ZFast<S, MODE>::v ? 3 : 4; };
+
 template <class S, int MODE>
-__global__ void __launch_bounds__(256) k_zsolve(const ZArgs a) {
+__global__ void __launch_bounds__(256, (ZMinBlocks<S, MODE>::v)) k_zsolve(const ZArgs a) {
   long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= a.nreal) return;
   // slot s of the (padded) spectral plane -> row, column; padding columns carry no mode
@@ -121,14 +130,22 @@ __global__ void __launch_bounds__(256) k_zsolve(const ZArgs a) {
     zload<ZU>(cur, base, P, 0, 1, n);
     for (int k0 = 0; k0 < n; k0 += ZU) {
       if (k0 + ZU < n) zload<ZU>(nxt, base, P, k0 + ZU, 1, n);
+      if (ZFast<S, MODE>::v && k0 >= wlen && k0 >= qlen && k0 + ZU < n) {
 #pragma unroll
-      for (int u = 0; u < ZU; u++) {
-        const int k = k0 + u;
-        if (k < n) {
-          df d = zcvt(cur[u]) * scale;
-          g = (d - g) * W(k);
-          if (periodic && k < qlen) y0 = y0 + f2df(__ldg(qt + k)) * d;
-          zput(base + k * P, g);
+        for (int u = 0; u < ZU; u++) {
+          g = (zcvt(cur[u]) * scale - g) * winf;
+          zput(base + (k0 + u) * P, g);
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < ZU; u++) {
+          const int k = k0 + u;
+          if (k < n) {
+            df d = zcvt(cur[u]) * scale;
+            g = (d - g) * W(k);
+            if (periodic && k < qlen) y0 = y0 + f2df(__ldg(qt + k)) * d;
+            zput(base + k * P, g);
+          }
         }
       }
 #pragma unroll
@@ -145,6 +162,21 @@ __global__ void __launch_bounds__(256) k_zsolve(const ZArgs a) {
     zload<ZU>(cur, base, P, n - 1, -1, n);
     for (int k0 = n - 1; k0 >= 0; k0 -= ZU) {
       if (k0 - ZU >= 0) zload<ZU>(nxt, base, P, k0 - ZU, -1, n);
+      if (ZFast<S, MODE>::v && k0 - ZU + 1 >= wlen && k0 - ZU + 1 >= qlen && k0 < n - 1) {
+#pragma unroll
+        for (int t = 0; t < ZU; t++) {
+          u = zcvt(cur[t]) - winf * u;
+          if (periodic) {
+            p = -(winf * p);
+            zput(base + (k0 - t) * P, u - c * p);
+          } else {
+            zput(base + (k0 - t) * P, u);
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < ZU; t++) cur[t] = nxt[t];
+        continue;
+      }
 #pragma unroll
       for (int t = 0; t < ZU; t++) {
         const int k = k0 - t;
