@@ -297,7 +297,8 @@ static pp_status z_tables(pp_plan* p) {
         b_last = b_int - h2 * h2 / gamma;
         m.flags = ZF_PERIODIC;
         thomas_multipliers(nz, h2, b_first, b_int, b_last, ws);
-        // q = h2 A'^{-1} e_0 (forward elimination of e_0 decays; truncate when negligible)
+        // q = h2 A'^{-1} e_0 (forward elimination of e_0 decays geometrically; truncated once below
+        // 2^-64 of its first entry, 2^-16 under the double-float rounding of the terms it enters)
         dp.assign(nz, 0.0);
         cpv.assign(nz, 0.0);
         auto wk = [&](int k) { return k == nz - 1 ? ws.wlast : (k < (int)ws.pre.size() ? ws.pre[k] : ws.winf); };
@@ -306,7 +307,7 @@ static pp_status z_tables(pp_plan* p) {
           // dp_k = (e0_k - h2 dp_{k-1}) / m_k,  1/m_k = w_k / h2
           double rhs = (k == 0) ? 1.0 : -h2 * dp[k - 1];
           dp[k] = rhs * wk(k) / h2;
-          if (k > 0 && std::fabs(dp[k]) < 1e-40 * std::fabs(dp[0])) { K = k; break; }
+          if (k > 0 && std::fabs(dp[k]) < 0x1p-64 * std::fabs(dp[0])) { K = k; break; }
         }
         // back substitution x_k = dp_k - cp_k x_{k+1}, cp_k = w_k
         std::vector<double> q(K);

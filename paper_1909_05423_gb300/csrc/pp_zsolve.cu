@@ -18,9 +18,10 @@
 //     x = y - c z,  y = A'^{-1} d,  z = A'^{-1} u = gamma q + p,
 //     c = (y_0 + y_{n-1}/gamma) / (1 + z_0 + z_{n-1}/gamma).
 // y_0 = sum_k q_k d_k (q = A'^{-1} e_0 = first row of the symmetric A'^{-1}) is accumulated in
-// the forward sweep from a stored prefix of q, p = A'^{-1} e_{n-1} is generated in the
-// backward sweep (p_{n-1} = w_{n-1}, p_k = -w_k p_{k+1}), so the cyclic solve also takes two
-// sweeps.
+// the forward sweep from a stored prefix of q.  p = A'^{-1} e_{n-1} satisfies p_{n-1} = w_{n-1},
+// p_k = -w_k p_{k+1}, so v = y - c p obeys the back substitution itself,
+//     v_k = g_k - w_k v_{k+1},  v_{n-1} = g_{n-1} - c w_{n-1},
+// and x_k = v_k - c gamma q_k: the cyclic solve takes the two Thomas sweeps plus the q prefix.
 //
 // The singular mode of a problem without Dirichlet faces (Sec. "Well-posedness") removes the
 // source mean, pins u_0 = 0, solves rows 1..n-1, and shifts the result to zero mean.
@@ -86,9 +87,12 @@ __device__ __noinline__ void z_singular(S* base, long long P, int n, df scale, c
 // by instruction issue, the FP32 spill and the cyclic double-float sweeps (measured), and not in
 // the Thomas double-float sweeps, which run at the copy bandwidth without it.
 template <class S, int MODE> struct ZFast { static constexpr bool v = sizeof(S) == 4 || MODE == 1; };
-// CTAs of 256 threads per SM the register allocation must allow: 4 (64 registers) for the
-// Thomas double-float sweeps, 3 (85) where the batches have a fast path.
-template <class S, int MODE> struct ZMinBlocks { static constexpr int v = ZFast<S, MODE>::v ? 3 : 4; };
+// CTAs of 256 threads per SM the register allocation must allow (measured): 4 (64 registers)
+// for the Thomas double-float sweeps, 3 (85) where the batches have a fast path, 2 for the cyclic
+// FP32-spill sweeps (at 85 they spill).
+template <class S, int MODE> struct ZMinBlocks {
+  static constexpr int v = (MODE == 1 && sizeof(S) == 4) ? 2 : (ZFast<S, MODE>::v ? 3 : 4);
+};
 
 template <class S, int MODE>
 __global__ void __launch_bounds__(256, (ZMinBlocks<S, MODE>::v)) k_zsolve(const ZArgs a) {
@@ -151,14 +155,13 @@ __global__ void __launch_bounds__(256, (ZMinBlocks<S, MODE>::v)) k_zsolve(const 
 #pragma unroll
       for (int u = 0; u < ZU; u++) cur[u] = nxt[u];
     }
-    // back substitution u_k = g_k - w_k u_{k+1}
-    df c = df{0.f, 0.f}, gam = df{0.f, 0.f};
+    // back substitution u_k = g_k - w_k u_{k+1} (periodic: v_k, see the header)
+    df c = df{0.f, 0.f}, cg = df{0.f, 0.f};
     if (periodic) {
-      gam = f2df(m.gam);
       c = (y0 + g * f2df(m.igam)) * f2df(m.dsm);  // g == y_{n-1}
+      cg = c * f2df(m.gam);
     }
     df u = df{0.f, 0.f};
-    df p = wlast;
     zload<ZU>(cur, base, P, n - 1, -1, n);
     for (int k0 = n - 1; k0 >= 0; k0 -= ZU) {
       if (k0 - ZU >= 0) zload<ZU>(nxt, base, P, k0 - ZU, -1, n);
@@ -166,12 +169,7 @@ __global__ void __launch_bounds__(256, (ZMinBlocks<S, MODE>::v)) k_zsolve(const 
 #pragma unroll
         for (int t = 0; t < ZU; t++) {
           u = zcvt(cur[t]) - winf * u;
-          if (periodic) {
-            p = -(winf * p);
-            zput(base + (k0 - t) * P, u - c * p);
-          } else {
-            zput(base + (k0 - t) * P, u);
-          }
+          zput(base + (k0 - t) * P, u);
         }
 #pragma unroll
         for (int t = 0; t < ZU; t++) cur[t] = nxt[t];
@@ -181,16 +179,11 @@ __global__ void __launch_bounds__(256, (ZMinBlocks<S, MODE>::v)) k_zsolve(const 
       for (int t = 0; t < ZU; t++) {
         const int k = k0 - t;
         if (k >= 0) {
-          const df wk = W(k);
           const df gk = zcvt(cur[t]);
-          u = (k == n - 1) ? gk : gk - wk * u;
+          if (k == n - 1) u = periodic ? gk - c * wlast : gk;
+          else u = gk - W(k) * u;
           df outv = u;
-          if (periodic) {
-            if (k < n - 1) p = -(wk * p);
-            df zk = p;
-            if (k < qlen) zk = zk + gam * f2df(__ldg(qt + k));
-            outv = u - c * zk;
-          }
+          if (periodic && k < qlen) outv = u - cg * f2df(__ldg(qt + k));
           zput(base + k * P, outv);
         }
       }

@@ -98,6 +98,18 @@ def test_exact_discrete_eigenfunction():
     assert rel_l2(u, u_star * ratio) <= TOL_F64
 
 
+@pytest.mark.parametrize("shape,bc", [((1024, 4, 6), "DDNNPP"), ((700, 8, 16), "PPPPPP"), ((512, 6, 4), "NNNNPP")])
+def test_periodic_z_long_lines(oracle, shape, bc):
+    """Cyclic z solves of long lines, where the first row of the inverse (the Sherman-Morrison q
+    vector) decays slowly for the low modes and is stored only up to 2^-64 of its first entry."""
+    nz, ny, nx = shape
+    sp = (1.0 / nx, 1.0 / ny, 1.0 / nz)
+    f = workloads.uniform_source(shape, seed=13, remove_mean=False)
+    ref = oracle.solve(f, bc, sp)
+    assert rel_l2(gpu_solve(f, bc, sp), ref) <= TOL_F64
+    assert rel_l2(gpu_solve(f, bc, sp, "mixed_f64io"), ref) <= 1e-6
+
+
 def test_singular_zero_mean(oracle):
     shape = (16, 24, 36)
     rng = np.random.default_rng(5)
