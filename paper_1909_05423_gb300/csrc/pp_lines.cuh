@@ -217,6 +217,33 @@ __device__ __forceinline__ void for_items_xb(int nl, LD&& ld, ST&& st) {
   }
 }
 
+// y tiles of the compile-time power-of-two kernels: when the tile is full and the CTA has one
+// thread per (group, k0), k0 < KS, every thread takes the items k0 + KS i (compile-time i) of its
+// group, with no division and no bounds or partial-group tests; the Hermitian-pair kinds
+// (KC = M/2 + 1 items) add the middle item k = M/2.  Other tiles take for_groups.
+template <class R, int MC, int V, int KC, class F>
+__device__ __forceinline__ void for_groups_y(const LineArgs& a, int nl, const FastDiv& fdk, F&& fn) {
+  if constexpr (MC >= 64 && (MC & (MC - 1)) == 0) {
+    constexpr int VPT = ct_values_per_thread(MC, true, std::is_same<R, df>::value);
+    constexpr int KS = V * (MC / VPT);
+    constexpr int NI = MC / KS;
+    static_assert(KC == MC || KC == MC / 2 + 1, "item counts of the y kinds");
+    static_assert(NI % 2 == 0, "half of a thread's items lie below M/2");
+    const int G = a.lpc / V;
+    if (nl == a.lpc && (G & (G - 1)) == 0 && (int)blockDim.x == KS * G) {
+      const int lg = __ffs(G) - 1;
+      const int L0 = ((int)threadIdx.x & (G - 1)) * V;
+      const int k0 = (int)threadIdx.x >> lg;
+      constexpr int NF = (KC == MC) ? NI : NI / 2;
+#pragma unroll
+      for (int i = 0; i < NF; i++) fn(L0, k0 + KS * i, V);
+      if (KC != MC && k0 == 0) fn(L0, MC / 2, V);
+      return;
+    }
+  }
+  for_groups<V, KC>(a, nl, fdk, fn);
+}
+
 template <class R, class SI> struct SrcGlobal {
   using elem_t = SI;
   const SI* in;
@@ -324,7 +351,7 @@ __device__ __noinline__ void pre_tile(const LineArgs& a, const Src src, int nl, 
       const long long pos = src.pos;
       if (kind == LK_DCT2 || kind == LK_DST2) {
         const bool dst = (kind == LK_DST2);
-        for_groups<V, MC>(a, nl, fk, [&](int L0, int k, int nv) {
+        for_groups_y<R, MC, V, MC>(a, nl, fk, [&](int L0, int k, int nv) {
           const long long b = src.base(L0);
           const int j0 = 2 * k, j1 = 2 * k + 1;
           const int s0 = j0 < M ? 2 * j0 : 2 * N - 1 - 2 * j0;
@@ -364,7 +391,7 @@ __device__ __noinline__ void pre_tile(const LineArgs& a, const Src src, int nl, 
         // as the scalar Hermitian-pair path below, V lines per item
         const cx<R>* w4 = aux + (M + 1);
         const bool c3 = (kind == LK_DCT3);
-        for_groups<V, (MC ? MC / 2 + 1 : 0)>(a, nl, fk, [&](int L0, int k, int nv) {
+        for_groups_y<R, MC, V, (MC ? MC / 2 + 1 : 0)>(a, nl, fk, [&](int L0, int k, int nv) {
           const long long b = src.base(L0);
           auto row = [&](int j) -> long long { return (long long)(c3 ? j : N - 1 - j) * pos; };
           R y0[V], y1[V], y2[V], y3[V];  // Y_k, Y_{N-k} (Y_N = 0), Y_{M-k}, Y_{M+k}
@@ -541,7 +568,7 @@ __device__ __noinline__ void post_tile(const LineArgs& a, const cx<R>* buf, int 
       if (kind == LK_DCT2 || kind == LK_DST2) {
         // as the scalar Hermitian-pair path below, V lines per item
         const bool dst = (kind == LK_DST2);
-        for_groups<V, (MC ? MC / 2 + 1 : 0)>(a, nl, fk, [&](int L0, int k, int nv) {
+        for_groups_y<R, MC, V, (MC ? MC / 2 + 1 : 0)>(a, nl, fk, [&](int L0, int k, int nv) {
           const long long b = s_bout[L0];
           const int km = M - k;
           const cx<R> ak = aux[k], wk = aux[M + 1 + k], wm = aux[M + 1 + km];
@@ -576,7 +603,7 @@ __device__ __noinline__ void post_tile(const LineArgs& a, const cx<R>* buf, int 
       }
       if (kind == LK_DCT3 || kind == LK_DST3) {
         const bool dst = (kind == LK_DST3);
-        for_groups<V, MC>(a, nl, fk, [&](int L0, int k, int nv) {
+        for_groups_y<R, MC, V, MC>(a, nl, fk, [&](int L0, int k, int nv) {
           const long long b = s_bout[L0];
           const int j0 = 2 * k, j1 = 2 * k + 1;
           const int s0 = j0 < M ? 2 * j0 : 2 * N - 1 - 2 * j0;

@@ -303,3 +303,19 @@ def test_maximum_line_lengths(oracle, shape, bc):
     for dtype, tol in (("f64", TOL_F64), ("mixed_f64io", 1e-6)):
         u = gpu_solve(f, bc, sp, dtype)
         assert rel_l2(u, ref) <= tol, (dtype, rel_l2(u, ref))
+
+
+@pytest.mark.parametrize("shape", [(3, 1024, 8), (3, 512, 16), (3, 256, 10), (4, 128, 12)])
+@pytest.mark.parametrize("bc", ["NNDDNN", "DDNNPP", "PPNNDD", "NNDDPP"])
+@pytest.mark.parametrize("shape_opt", [None, dict(threads_y=256, cols_y=8, threads_y_inv=256, cols_y_inv=8)])
+def test_y_power_of_two_tiles(oracle, shape, bc, shape_opt):
+    """y lines of 128..1024 reals (compile-time FFT lengths 64..512) in full tiles, where each thread
+    takes a fixed set of items per tile, and in partial last tiles (nx = 10, 12), which take the
+    general loop; forward (DST-II / DCT-II) and inverse (DST-III / DCT-III) kinds, FP64 and mixed."""
+    nz, ny, nx = shape
+    sp = (1.0 / nx, 1.0 / ny, 1.0 / nz)
+    f = workloads.uniform_source(shape, seed=41)
+    ref = oracle.solve(f, bc, sp)
+    for dtype, tol in (("f64", TOL_F64), ("mixed_f64io", 1e-6)):
+        u = gpu_solve(f, bc, sp, dtype, options=shape_opt)
+        assert rel_l2(u, ref) <= tol, (dtype, rel_l2(u, ref))
