@@ -198,6 +198,33 @@ __device__ __forceinline__ void for_groups(const LineArgs& a, int nl, const Fast
 // take half as well).
 constexpr int pre_batch(int MC, int full) { return (MC >= 256 && (MC & (MC - 1)) == 0) ? full : (full > 1 ? full / 2 : 1); }
 
+// x tiles of the compile-time power-of-two kernels: when the tile is full and the CTA has one
+// team of TPL threads per line, thread k0 of line L takes the items k0 + TPL i (compile-time i);
+// KC = M/2 + 1 adds the middle item k = M/2.  XTeam::ok(a, nl) tells whether the tile qualifies.
+template <class R, int MC> struct XTeam {
+  static constexpr bool ct = MC >= 64 && (MC & (MC - 1)) == 0;
+  static constexpr int TPL = ct ? MC / ct_values_per_thread(MC, false, std::is_same<R, df>::value) : 1;
+  __device__ static __forceinline__ bool ok(const LineArgs& a, int nl) {
+    return ct && nl == a.lpc && (int)blockDim.x == TPL * a.lpc;
+  }
+};
+template <class R, bool OY, int MC, int KC, class F>
+__device__ __forceinline__ void for_items_x(const LineArgs& a, int nl, const FastDiv& fdk, F&& fn) {
+  if constexpr (!OY && XTeam<R, MC>::ct) {
+    constexpr int TPL = XTeam<R, MC>::TPL;
+    static_assert(KC == MC || KC == MC / 2 || KC == MC / 2 + 1, "item counts of the x kinds");
+    if (XTeam<R, MC>::ok(a, nl)) {
+      const int L = (int)threadIdx.x / TPL, k0 = (int)threadIdx.x % TPL;
+      constexpr int NF = (KC == MC) ? MC / TPL : MC / 2 / TPL;
+#pragma unroll
+      for (int i = 0; i < NF; i++) fn(L, k0 + TPL * i);
+      if (KC == MC / 2 + 1 && k0 == 0) fn(L, MC / 2);
+      return;
+    }
+  }
+  for_items<OY, KC>(a, nl, fdk, fn);
+}
+
 template <int KC, int U, class LD, class ST>
 __device__ __forceinline__ void for_items_xb(int nl, LD&& ld, ST&& st) {
   const int tot = nl * KC;
@@ -244,6 +271,33 @@ __device__ __forceinline__ void for_groups_y(const LineArgs& a, int nl, const Fa
   for_groups<V, KC>(a, nl, fdk, fn);
 }
 
+// for_items_xb with the team mapping of for_items_x where the tile qualifies (U | the item count).
+// Used by the forward x kinds; the inverse kinds' loops measured slower with it (larger code in the
+// kernel that also converts to FP64).
+template <class R, int MC, int KC, int U, class LD, class ST>
+__device__ __forceinline__ void for_items_xbt(const LineArgs& a, int nl, LD&& ld, ST&& st) {
+  if constexpr (XTeam<R, MC>::ct) {
+    constexpr int TPL = XTeam<R, MC>::TPL;
+    constexpr int NF = MC / 2 / TPL;
+    static_assert(KC == MC / 2 || KC == MC / 2 + 1, "item counts of the batched x kinds");
+    static_assert(NF % U == 0, "whole batches");
+    if (XTeam<R, MC>::ok(a, nl)) {
+      const int L = (int)threadIdx.x / TPL, k0 = (int)threadIdx.x % TPL;
+#pragma unroll
+      for (int i0 = 0; i0 < NF; i0 += U) {
+        decltype(ld(0, 0)) r[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) r[u] = ld(L, k0 + TPL * (i0 + u));
+#pragma unroll
+        for (int u = 0; u < U; u++) st(L, k0 + TPL * (i0 + u), r[u]);
+      }
+      if (KC == MC / 2 + 1 && k0 == 0) st(L, MC / 2, ld(L, MC / 2));
+      return;
+    }
+  }
+  for_items_xb<KC, U>(nl, ld, st);
+}
+
 template <class R, class SI> struct SrcGlobal {
   using elem_t = SI;
   const SI* in;
@@ -272,8 +326,8 @@ __device__ __noinline__ void pre_tile(const LineArgs& a, const Src src, int nl, 
         const bool dst = (kind == LK_DST2);
         using raw_t = typename Vec<R, SI>::raw_t;
         struct Raw { raw_t a, b; };
-        for_items_xb<MC / 2, pre_batch(MC, std::is_same<R, df>::value ? 4 : 2)>(
-            nl,
+        for_items_xbt<R, MC, MC / 2, pre_batch(MC, std::is_same<R, df>::value ? 4 : 2)>(
+            a, nl,
             [&](int L, int k) {
               const long long b = src.base(L) + 4LL * k;
               return Raw{Vec<R, SI>::raw(src.in, b), Vec<R, SI>::raw(src.in, b + 2)};
@@ -648,7 +702,7 @@ __device__ __noinline__ void post_tile(const LineArgs& a, const cx<R>* buf, int 
       // O_{M-k} = conj O_k and w_N^{M-k} = -conj w_N^k give X_{M-k} = conj(E_k - w_N^k O_k); item
       // k <= M/2 emits X_k and X_{M-k} (k = 0: X_0 and X_M).  DCT-II: W = exp(-i pi k/2N) X_k,
       // Y_k = Re W, Y_{N-k} = -Im W; DST-II writes the DCT-II of the sign-alternated line reversed.
-      for_items<OY, (MC ? MC / 2 + 1 : 0)>(a, nl, fk, [&](int L, int k) {
+      for_items_x<R, OY, MC, (MC ? MC / 2 + 1 : 0)>(a, nl, fk, [&](int L, int k) {
         const long long b = s_bout[L];
         const cx<R>* zl = buf + L * ldm;
         const int km = M - k;

@@ -319,3 +319,21 @@ def test_y_power_of_two_tiles(oracle, shape, bc, shape_opt):
     for dtype, tol in (("f64", TOL_F64), ("mixed_f64io", 1e-6)):
         u = gpu_solve(f, bc, sp, dtype, options=shape_opt)
         assert rel_l2(u, ref) <= tol, (dtype, rel_l2(u, ref))
+
+
+@pytest.mark.parametrize("shape", [(3, 8, 1024), (3, 16, 512), (3, 10, 256), (3, 14, 128)])
+@pytest.mark.parametrize("bc", ["NNDDNN", "DDNNPP", "NDNDDD"])
+@pytest.mark.parametrize("shape_opt", [None, dict(threads_x=256, lines_x=4, threads_x_inv=256, lines_x_inv=4),
+                                       dict(threads_x=128, lines_x=2, threads_x_inv=128, lines_x_inv=2)])
+def test_x_power_of_two_tiles(oracle, shape, bc, shape_opt):
+    """x lines of 128..1024 reals (compile-time FFT lengths 64..512) in full tiles, where each line's
+    team of threads takes a fixed set of items, and in tiles whose last one is partial (ny nz not a
+    multiple of the lines per CTA); DCT-II/DST-II forward, DCT-III/DST-III inverse, type IV for the
+    mixed faces, FP64 and mixed."""
+    nz, ny, nx = shape
+    sp = (1.0 / nx, 1.0 / ny, 1.0 / nz)
+    f = workloads.uniform_source(shape, seed=43)
+    ref = oracle.solve(f, bc, sp)
+    for dtype, tol in (("f64", TOL_F64), ("mixed_f64io", 1e-6)):
+        u = gpu_solve(f, bc, sp, dtype, options=shape_opt)
+        assert rel_l2(u, ref) <= tol, (dtype, rel_l2(u, ref))
