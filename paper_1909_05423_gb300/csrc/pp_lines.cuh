@@ -774,8 +774,8 @@ __device__ __noinline__ void post_tile(const LineArgs& a, const cx<R>* buf, int 
 }
 
 // Register caps (measured): FP32 48 (ten 128-thread CTAs per SM); double-float 64 (eight), except
-// the warp-per-line y kernels of 512-point lines, which hold 16 values per thread (80: one of them
-// spills 112 bytes per thread and is still faster than at 96 or 72).  None of the other
+// the warp-per-line y kernels of 512-point lines, which hold 16 values per thread (80: the
+// double-float one spills 144 bytes per thread and is still faster than at 96 or 72).  None of the other
 // compile-time-length kernels spills.  The run-time-length kernels get 64 (FP32) and 128
 // (double-float).
 template <class R, int MC, bool OY> struct MaxRegs {
