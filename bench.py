@@ -65,13 +65,22 @@ KERNEL_SOURCES = ("pp_arith.cuh", "pp_fft.cuh", "pp_internal.h", "pp_lines.cuh",
                   "pp_lines_df_ct3b.cu", "pp_lines_f32_ct3a.cu", "pp_lines_f32_ct3b.cu", "pp_zsolve.cu", "pp_misc.cu")
 
 
+def _code_only(text: str) -> str:
+    """C/C++ source without comments and with whitespace runs collapsed (a comment edit leaves
+    the kernels, and so the hash, unchanged)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def _source_hash():
-    """Hash of the kernel sources (the traffic figures in profiles/ are valid only for these)."""
+    """Hash of the kernel sources' code (the traffic figures in profiles/ are valid only for these)."""
     import hashlib
     h = hashlib.sha256()
     for name in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1909_05423_gb300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1909_05423_gb300", "csrc", name), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 
