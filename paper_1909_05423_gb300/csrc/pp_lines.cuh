@@ -366,7 +366,7 @@ __device__ __noinline__ void pre_tile(const LineArgs& a, const Src src, int nl, 
       }
     }
     if (kind == LK_DCT3 || kind == LK_DST3) {
-      // as the Hermitian-pair path below, with the four loads of two items issued together
+      // as the Hermitian-pair path below, with the four loads of up to two items issued together
       const cx<R>* w4 = aux + (M + 1);
       const bool c3 = (kind == LK_DCT3);
       struct Raw { SI y0, y1, y2, y3; };  // Y_k, Y_{N-k} (Y_N = 0), Y_{M-k}, Y_{M+k}
