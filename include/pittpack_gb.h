@@ -102,7 +102,12 @@ pp_status pp_plan_create(pp_plan** out, int nx, int ny, int nz, const pp_bc bc[6
 /* Solve A u = f (Secs. "Boundary Conditions" to "Solution of the Resulting Tridiagonal
  * Matrices").  f_dev, u_dev: device arrays of nx*ny*nz doubles (PP_F64, PP_MIXED_F64IO)
  * or floats (PP_MIXED_F32IO), owned by the caller; u may alias f.  Asynchronous on
- * stream.  Errors: PP_ERR_INVALID_ARG (NULL plan/pointer), PP_ERR_CUDA (launch). */
+ * stream.  Errors: PP_ERR_INVALID_ARG (NULL plan/pointer), PP_ERR_CUDA (launch).
+ * Range: the double-float arithmetic has FP32's exponent range.  Sources and solutions with
+ * magnitudes between about 1e-25 and 1e30 (the transforms sum up to n values, the z solve
+ * divides by dz^2) keep the full ~47-bit accuracy; values beyond about 3e38 overflow to
+ * infinity and values below about 1e-38 are flushed to zero.  The problem is linear: scale f
+ * by a power of two into that range and u back by the same factor. */
 pp_status pp_solve(pp_plan* plan, const void* f_dev, void* u_dev, pp_stream_t stream);
 
 /* Mixed precision with one FP64 residual-refinement step: u0 = solve(f),
