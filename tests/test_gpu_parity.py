@@ -337,3 +337,15 @@ def test_x_power_of_two_tiles(oracle, shape, bc, shape_opt):
     for dtype, tol in (("f64", TOL_F64), ("mixed_f64io", 1e-6)):
         u = gpu_solve(f, bc, sp, dtype, options=shape_opt)
         assert rel_l2(u, ref) <= tol, (dtype, rel_l2(u, ref))
+
+
+@pytest.mark.parametrize("scale", [1e-20, 1e25])
+def test_magnitude_range(oracle, scale):
+    """The double-float path has FP32's exponent range; sources scaled to 1e-20 and 1e25 (inside
+    the range the header states) keep FP64-class accuracy.  The problem is linear, so the
+    oracle's solution of the unscaled source, scaled, is the reference."""
+    shape = (12, 64, 256)
+    sp = (1.0 / 256, 1.0 / 64, 1.0 / 12)
+    f = workloads.uniform_source(shape, seed=47)
+    ref = oracle.solve(f, "NNDDNN", sp) * scale
+    assert rel_l2(gpu_solve(f * scale, "NNDDNN", sp), ref) <= TOL_F64
