@@ -21,7 +21,8 @@ def lib():
 def _declared():
     names = set()
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
-        txt = open(h).read()
+        with open(h) as fh:
+            txt = fh.read()
         txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
         names.update(re.findall(r"\b(pp_[a-z_0-9]+)\s*\(", txt))
     return sorted(names)

@@ -18,7 +18,9 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "mms_tables.txt")
 
 def _golden_rows():
     rows = []
-    for line in open(GOLDEN):
+    with open(GOLDEN) as fh:
+        lines = fh.read().splitlines()
+    for line in lines:
         line = line.strip()
         if not line or line.startswith("#"):
             continue
