@@ -477,6 +477,11 @@ def run_ours(args):
         variants["mixed_f64io"] = {"value": npts / (ms_m * 1e-3) / 1e9, "ms_per_step": ms_m,
                                    "stage_ms": dict(zip(STAGES, per_m)), "speedup_vs_f64": ms / ms_m,
                                    "rel_l2_vs_f64_path": err_m}
+        # mixed solve + one refinement step (exact residual, FP32 correction solve)
+        ms_r = _events_ms(lambda: pm.solve_refined(f, um), args.steps, warmup=args.warmup)
+        err_r = (torch.linalg.vector_norm(um - u) / torch.linalg.vector_norm(u)).item()
+        variants["refined_f64io"] = {"value": npts / (ms_r * 1e-3) / 1e9, "ms_per_step": ms_r,
+                                     "speedup_vs_f64": ms / ms_r, "rel_l2_vs_f64_path": err_r}
         pm.close()
         del um
 

@@ -63,7 +63,8 @@ typedef enum {
   PP_ERR_OUT_OF_MEMORY = 4,
   PP_ERR_CUDA = 5,
   PP_ERR_TIMEOUT = 6,
-  PP_ERR_INTERNAL = 7
+  PP_ERR_INTERNAL = 7,
+  PP_ERR_RANGE = 8 /* pp_plan_status only: values left the range of full accuracy (see there) */
 } pp_status;
 
 /* Optional plan settings; pass NULL for the defaults. */
@@ -105,15 +106,18 @@ pp_status pp_plan_create(pp_plan** out, int nx, int ny, int nz, const pp_bc bc[6
  * stream.  Errors: PP_ERR_INVALID_ARG (NULL plan/pointer), PP_ERR_CUDA (launch).
  * Range: the double-float arithmetic has FP32's exponent range.  Sources and solutions with
  * magnitudes between about 1e-25 and 1e30 (the transforms sum up to n values, the z solve
- * divides by dz^2) keep the full ~47-bit accuracy; values beyond about 3e38 overflow to
- * infinity and values below about 1e-38 are flushed to zero.  The problem is linear: scale f
+ * scales by dz^2 and the inverse weights) keep the full ~47-bit accuracy; a solve outside the
+ * range of full accuracy sets PP_ERR_RANGE in pp_plan_status().  The problem is linear: scale f
  * by a power of two into that range and u back by the same factor. */
 pp_status pp_solve(pp_plan* plan, const void* f_dev, void* u_dev, pp_stream_t stream);
 
-/* Mixed precision with one FP64 residual-refinement step: u0 = solve(f),
- * r = f - A u0 (7-point stencil of Sec. "Mathematical Formulation", evaluated in
- * double-float arithmetic), u = u0 + solve(r).  Only for PP_MIXED_F64IO plans
- * (PP_ERR_INVALID_ARG otherwise).  u must not alias f. */
+/* Mixed precision with one residual-refinement step: u0 = solve(f) (FP32 transforms, so u0 is
+ * FP32-exact), r = f - A u0 (7-point stencil of Sec. "Mathematical Formulation"; the second
+ * differences of u0 are formed exactly, then scaled by 1/h^2 and subtracted from f in double-float
+ * arithmetic, so r is accurate to ~2^-46 |f|), delta = solve(r) with FP32 I/O, u = u0 + delta
+ * (rounded once to FP64).  The error of u is about the square of the mixed solve's (~1e-13 against
+ * the exact discrete solution).  Only for PP_MIXED_F64IO plans (PP_ERR_INVALID_ARG otherwise).  u
+ * must not alias f.  The first call on a plan allocates a grid-sized FP32 scratch. */
 pp_status pp_solve_refined(pp_plan* plan, const void* f_dev, void* u_dev, pp_stream_t stream);
 
 /* pp_solve_refined without any device allocation.  (The paper has no counterpart: it is an
@@ -122,10 +126,11 @@ pp_status pp_solve_refined(pp_plan* plan, const void* f_dev, void* u_dev, pp_str
  * loops that must not allocate mid-run; applications whose own allocator owns the GPU.)
  * pp_solve_refined allocates a grid-sized residual buffer on its first call; this entry point
  * instead uses a fixed 16 MiB device array inside the library (held by every GPU that loads the
- * library until the process exits) plus the plan's own workspace.
+ * library until the process exits) plus the plan's own workspace.  Same arithmetic as
+ * pp_solve_refined, step for step.
  *   plan   : a PP_MIXED_F64IO plan (created beforehand; creating a plan does allocate)
  *   f_dev  : input, nx*ny*nz doubles on the device; u_dev: output, same size, must not alias f
- * Limit: nx*ny*nz <= 2,097,152 cells (16 MiB of FP64), else PP_ERR_UNSUPPORTED_SIZE with a
+ * Limit: nx*ny*nz <= 2,097,152 cells (the FP32 residual of such a grid), else PP_ERR_UNSUPPORTED_SIZE with a
  * message; other errors as pp_solve_refined.  The first call on each device looks up the
  * array's device address (cudaGetSymbolAddress), so make that first call before any stream
  * capture.  All calls share the one array and each call overwrites what it reads, so calls
@@ -195,8 +200,16 @@ pp_status pp_run_stage(pp_plan* plan, int stage, const void* f_dev, void* u_dev,
 /* Release the plan and its device memory (synchronises the device first). NULL is a no-op. */
 pp_status pp_plan_destroy(pp_plan* plan);
 
-/* Device-side status of the plan's last solves (PP_OK unless a kernel reported an error).
- * Call after synchronising the stream; reading clears it. */
+/* Device-side status of the plan's solves since the last call (PP_OK unless a kernel reported a
+ * condition).  Call after synchronising the stream; reading clears it.
+ *   PP_ERR_RANGE: in at least one solve (every launch of the z-solve decides on its own data) the
+ *     largest scaled right-hand side entering the tridiagonal solves was below 2^-100 (the
+ *     FP32-exponent arithmetic then loses accuracy, e.g. a unit-cube source of magnitude 1e-32 at
+ *     32^3), or the largest z-solve output exceeded 2^124 / (nx ny) (the inverse transforms may
+ *     overflow FP32's range, e.g. 1e37 at 32^3), or a non-finite value appeared.  The decision is
+ *     made on the largest magnitudes only, so small values beside large ones raise nothing.  Sources
+ *     whose every magnitude is below FP32's smallest subnormal (~1.4e-45) are read as zero.  The
+ *     problem is linear: scale f by a power of two and u back. */
 pp_status pp_plan_status(pp_plan* plan);
 
 /* Bytes of device memory held by the plan (workspace + tables). */

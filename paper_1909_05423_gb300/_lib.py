@@ -14,7 +14,9 @@ LIB_PATH = os.path.join(_HERE, "_build", "libpittpack_gb.so")
 
 PP_OK = 0
 STATUS_NAMES = {0: "PP_OK", 1: "PP_ERR_INVALID_ARG", 2: "PP_ERR_UNSUPPORTED_SIZE", 3: "PP_ERR_BC_PAIRING",
-                4: "PP_ERR_OUT_OF_MEMORY", 5: "PP_ERR_CUDA", 6: "PP_ERR_TIMEOUT", 7: "PP_ERR_INTERNAL"}
+                4: "PP_ERR_OUT_OF_MEMORY", 5: "PP_ERR_CUDA", 6: "PP_ERR_TIMEOUT", 7: "PP_ERR_INTERNAL",
+                8: "PP_ERR_RANGE"}
+PP_ERR_RANGE = 8
 BC_CODE = {"P": 0, "N": 1, "D": 2}
 DTYPES = {"f64": 0, "mixed_f64io": 1, "mixed_f32io": 2}
 

@@ -140,7 +140,13 @@ static __device__ __noinline__ df df_from_double_slow(double d) {
     r.lo = 0.0f;
     return r;
   }
-  if (ef < 1) { r.hi = __uint_as_float(sign); r.lo = 0.0f; return r; }
+  if (ef < 1) {
+    // below FP32's normal range: the nearest FP32 value (subnormal, or zero below ~1.4e-45), so
+    // that a source of tiny magnitude stays visible to the z solve's range report
+    r.hi = __double2float_rn(d);
+    r.lo = 0.0f;
+    return r;
+  }
   r.hi = __uint_as_float(sign | ((unsigned)ef << 23) | mh);
   if (ef >= 24) {
     unsigned base = sign | ((unsigned)(ef - 23) << 23);
@@ -152,7 +158,8 @@ static __device__ __noinline__ df df_from_double_slow(double d) {
 }
 
 // Split an FP64 value into hi + lo (hi = truncated 24-bit significand, lo = the next 23 bits),
-// using integer operations only.  |d| < 2^-103 keeps only hi; |d| < 2^-126 flushes to zero.
+// using integer operations only.  |d| < 2^-103 keeps only hi; |d| < 2^-126 becomes the nearest
+// FP32 subnormal (zero below 2^-150).
 __device__ __forceinline__ df df_from_double(double d) {
   const unsigned h32 = (unsigned)__double2hiint(d), l32 = (unsigned)__double2loint(d);
   const unsigned sign = h32 & 0x80000000u;
@@ -189,22 +196,13 @@ __device__ __forceinline__ double df_to_double(df v) {
   return __dadd_rn(double_from_f32(v.hi), double_from_f32(v.lo));
 }
 
-// General-case FP64 -> FP32; see f32_from_double.
-static __device__ __noinline__ float f32_from_double_slow(double d) {
-  unsigned long long b = (unsigned long long)__double_as_longlong(d);
-  unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
-  unsigned sign = h32 & 0x80000000u;
-  int e = (int)((h32 >> 20) & 0x7ffu);
-  int ef = e - 896;
-  if (ef >= 255) return __uint_as_float(sign | 0x7f800000u | (e == 0x7ff && ((h32 & 0xfffffu) | l32) ? 0x400000u : 0u));
-  if (ef < 1) return __uint_as_float(sign);
-  unsigned mag = ((unsigned)ef << 23) | ((h32 & 0xfffffu) << 3) | (l32 >> 29);
-  mag += (l32 >> 28) & 1u;  // round half away from zero; a carry into the exponent is correct
-  if (mag >= 0x7f800000u) mag = 0x7f800000u;
-  return __uint_as_float(sign | mag);
-}
+// General-case FP64 -> FP32 (zeros, subnormal results, overflow, inf, nan): the hardware
+// conversion, round to nearest even (the FP64-rate unit; this path is rare).
+static __device__ __noinline__ float f32_from_double_slow(double d) { return __double2float_rn(d); }
 
-// FP64 -> FP32 rounded to nearest (ties away), integer operations only.
+// FP64 -> FP32 rounded to nearest, integer operations only.  Ties round away from zero on the
+// normal-range path (a tie needs the 29 discarded bits to be exactly 1000...0; both neighbours are
+// half an ulp away).
 __device__ __forceinline__ float f32_from_double(double d) {
   const unsigned h32 = (unsigned)__double2hiint(d), l32 = (unsigned)__double2loint(d);
   const unsigned t = (h32 & 0x7fffffffu) - (896u << 20);

@@ -100,7 +100,15 @@ struct ZArgs {
   const float2* qtab;     // (hi, lo) periodic end-solution prefix
   float scale[2];         // dz^2 * inverse-transform weights (hi, lo)
   int transpose;          // 1: solve with the transposed factorisation (adjoint)
+  // range status (plan-owned words: [0] status bits, [1] largest |scaled input|, [2] largest |output|
+  // (FP32 bits), [3] count of finished blocks); the last block of a launch compares the maxima
+  // with dmin / umax and sets kStatusRange in [0]
+  unsigned* rstat;
+  float dmin;             // 2^-100: below it the double-float low parts are subnormal
+  float umax;             // 2^124 / (nx ny): above it the inverse transforms may overflow FP32
 };
+// status bits of a plan's device status word
+constexpr unsigned kStatusRange = 1u;
 
 }  // namespace pp
 
@@ -139,7 +147,7 @@ struct pp_plan {
   void* d_host_u;
   cudaStream_t host_cs[2];  // copy streams of host-buffer solves (created on first use)
   cudaEvent_t host_ev[2 * pp::kHostChunks + 3];  // per-chunk copy / compute events, start, two joins
-  int* d_status;
+  unsigned* d_status;  // 4 words: status bits, two running maxima and a block counter (ZArgs::rstat)
 };
 
 namespace pp {
@@ -158,6 +166,10 @@ cudaError_t launch_fill(void* x, long long n, bool f32, cudaStream_t st);
 // mean of an FP64 grid: nparts block sums into `partials` (nparts float2), result (hi,lo) into `mean`
 cudaError_t launch_mean(const pp_plan* p, const void* u, void* partials, int nparts, void* mean, cudaStream_t st);
 constexpr int kMeanParts = 1024;
+// the refined solve on caller-provided scratch (resid: nx*ny*nz floats; partials: kMeanParts float2;
+// mean: one float2)
+__attribute__((visibility("hidden"))) pp_status solve_refined_core(pp_plan* p, const void* f, void* u, void* resid,
+                                                                  void* partials, void* mean, cudaStream_t st);
 // record the calling thread's error detail (returned by pp_last_error_string) and return s
 __attribute__((visibility("hidden"))) pp_status set_last_error(pp_status s, const char* msg);
 }  // namespace pp

@@ -26,6 +26,7 @@
 // radices 2, 3, 4, 8; MC = -1: run-time length with radix-5/7 stages as well).
 #pragma once
 #include <algorithm>
+#include <atomic>
 #include <type_traits>
 
 #include "pp_internal.h"
@@ -849,12 +850,17 @@ __global__ void __maxnreg__((MaxRegs<R, MC, OY>::v)) k_lines(const LineArgs args
 template <class R, class SI, class SO, bool OY, int MC>
 cudaError_t launch_lines_k(const LineArgs& a, int threads, cudaStream_t st) {
   auto k = k_lines<R, SI, SO, OY, MC>;
-  // dynamic shared memory above 48 KB must be opted into; plans keep it <= 200 KB
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  // dynamic shared memory above 48 KB must be opted into, per device; plans keep it <= 200 KB.
+  // One bit per device ordinal (below 64; higher ordinals set the attribute on every launch).
+  static std::atomic<unsigned long long> attr_done{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+  if (!bit || !(attr_done.load(std::memory_order_acquire) & bit)) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
-    attr = true;
+    attr_done.fetch_or(bit, std::memory_order_release);
   }
   const size_t sm = ((size_t)a.lpc * a.ldm + (size_t)a.fp.M) * sizeof(cx<R>) + 2 * (size_t)a.lpc * sizeof(long long);
   k<<<a.ntiles, threads, sm, st>>>(a);

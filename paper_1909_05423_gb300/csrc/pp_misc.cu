@@ -1,8 +1,19 @@
 // pp_misc.cu -- residual and update kernels of the mixed-precision refinement step.
 //
-// r = f - A_h u with the cell-centred 7-point stencil (Sec. "Mathematical Formulation") and the
-// face ghost rules (periodic wrap, Neumann u[-1] = u[0], homogeneous Dirichlet u[-1] = -u[0]),
-// evaluated in double-float arithmetic on FP64 data; then u += delta.
+// r = f - A_h u0 with the cell-centred 7-point stencil (Sec. "Mathematical Formulation") and the
+// face ghost rules (periodic wrap, Neumann u[-1] = u[0], homogeneous Dirichlet u[-1] = -u[0]);
+// then u = u0 + delta with delta = solve(r).
+//
+// The first solve's u0 comes out of FP32 transforms, so every u0 value is an FP32 number.  The
+// kernels read u0 rounded to FP32 (the identity for such values), which makes the stencil's
+// second differences exact: with u0 in FP32, (m - c) and (p - c) are each an exact sum of two
+// FP32 numbers (TwoSum), and their sum is formed in double-float to ~2^-48 of the difference
+// itself.  Only then are the three differences scaled by 1/h^2 and subtracted from f.  Formed the
+// other way round (each neighbour scaled, the sum taken after), the second difference inherits an
+// error of ~2^-48 |u| -- 1/(kappa h)^2 times its own size for a smooth u -- which bounded the
+// refined solution near 2e-12 at 512^3; with exact differences the residual is accurate to
+// ~2^-46 |f| and one step reaches ~1e-13.  r and delta are stored as FP32: r is the input of an
+// FP32-transform solve, and delta is ~1e-7 of u.
 #include "pp_internal.h"
 
 namespace pp {
@@ -10,50 +21,65 @@ namespace pp {
 struct ResArgs {
   const double* f;
   const double* u;
-  double* r;
+  float* r;
   int nx, ny, nz;
   int bc[6];
   float ix2[2], iy2[2], iz2[2];  // 1/h^2 as (hi, lo)
+  FastDiv fd_ny;                 // row -> (k, j)
 };
 
-__device__ __forceinline__ df ghost_or(int bc, df c) { return bc == 1 ? c : -c; }
+// ghost value of a homogeneous face (1 = Neumann: copy; 2 = Dirichlet: negate)
+__device__ __forceinline__ float ghost_or(int bc, float c) { return bc == 1 ? c : -c; }
 
-__global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
-  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  long long nxy = (long long)a.nx * a.ny;
-  long long n = nxy * a.nz;
-  if (p >= n) return;
-  int k = (int)(p / nxy);
-  long long rem = p - (long long)k * nxy;
-  int j = (int)(rem / a.nx);
-  int i = (int)(rem - (long long)j * a.nx);
-  const double* u = a.u;
-  df c = df_from_double(__ldg(u + p));
-  df xm, xp, ym, yp, zm, zp;
-  if (i > 0) xm = df_from_double(__ldg(u + p - 1));
-  else xm = (a.bc[0] == 0) ? df_from_double(__ldg(u + p + a.nx - 1)) : ghost_or(a.bc[0], c);
-  if (i < a.nx - 1) xp = df_from_double(__ldg(u + p + 1));
-  else xp = (a.bc[1] == 0) ? df_from_double(__ldg(u + p - (a.nx - 1))) : ghost_or(a.bc[1], c);
-  if (j > 0) ym = df_from_double(__ldg(u + p - a.nx));
-  else ym = (a.bc[2] == 0) ? df_from_double(__ldg(u + p + (long long)(a.ny - 1) * a.nx)) : ghost_or(a.bc[2], c);
-  if (j < a.ny - 1) yp = df_from_double(__ldg(u + p + a.nx));
-  else yp = (a.bc[3] == 0) ? df_from_double(__ldg(u + p - (long long)(a.ny - 1) * a.nx)) : ghost_or(a.bc[3], c);
-  if (k > 0) zm = df_from_double(__ldg(u + p - nxy));
-  else zm = (a.bc[4] == 0) ? df_from_double(__ldg(u + p + (long long)(a.nz - 1) * nxy)) : ghost_or(a.bc[4], c);
-  if (k < a.nz - 1) zp = df_from_double(__ldg(u + p + nxy));
-  else zp = (a.bc[5] == 0) ? df_from_double(__ldg(u + p - (long long)(a.nz - 1) * nxy)) : ghost_or(a.bc[5], c);
-  df c2 = c + c;
-  df lap = ((xm + xp) - c2) * df{a.ix2[0], a.ix2[1]} + ((ym + yp) - c2) * df{a.iy2[0], a.iy2[1]} +
-           ((zm + zp) - c2) * df{a.iz2[0], a.iz2[1]};
-  df r = df_from_double(__ldg(a.f + p)) - lap;
-  a.r[p] = df_to_double(r);
+// (m - c) + (p - c) for FP32 m, c, p: each difference exactly as an unevaluated pair (TwoSum), the
+// two pairs summed in double-float (relative error ~2^-48 of the result)
+__device__ __forceinline__ df second_difference(float m, float c, float p) {
+  df d1, d2;
+  two_sum(m, -c, d1.hi, d1.lo);
+  two_sum(p, -c, d2.hi, d2.lo);
+  return d1 + d2;
 }
 
-// u += d (- shift, the mean of u, when the problem is singular and the result must be mean-free)
-__global__ void __launch_bounds__(256) k_add(double* u, const double* d, long long n, const float2* shift) {
+__device__ __forceinline__ float u32(const double* u, long long i) { return f32_from_double(__ldg(u + i)); }
+
+// One x-row per blockIdx.x (rows = ny nz < 2^31), x positions over threads and blockIdx.y.
+__global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
+  const int i = (int)(blockIdx.y * blockDim.x + threadIdx.x);
+  if (i >= a.nx) return;
+  const unsigned row = blockIdx.x;
+  const int k = (int)a.fd_ny.div(row);
+  const int j = (int)(row - (unsigned)k * (unsigned)a.ny);
+  const long long nxy = (long long)a.nx * a.ny;
+  const long long p = (long long)row * a.nx + i;
+  const double* u = a.u;
+  const float c = u32(u, p);
+  float xm, xp, ym, yp, zm, zp;
+  if (i > 0) xm = u32(u, p - 1);
+  else xm = (a.bc[0] == 0) ? u32(u, p + a.nx - 1) : ghost_or(a.bc[0], c);
+  if (i < a.nx - 1) xp = u32(u, p + 1);
+  else xp = (a.bc[1] == 0) ? u32(u, p - (a.nx - 1)) : ghost_or(a.bc[1], c);
+  if (j > 0) ym = u32(u, p - a.nx);
+  else ym = (a.bc[2] == 0) ? u32(u, p + (long long)(a.ny - 1) * a.nx) : ghost_or(a.bc[2], c);
+  if (j < a.ny - 1) yp = u32(u, p + a.nx);
+  else yp = (a.bc[3] == 0) ? u32(u, p - (long long)(a.ny - 1) * a.nx) : ghost_or(a.bc[3], c);
+  if (k > 0) zm = u32(u, p - nxy);
+  else zm = (a.bc[4] == 0) ? u32(u, p + (long long)(a.nz - 1) * nxy) : ghost_or(a.bc[4], c);
+  if (k < a.nz - 1) zp = u32(u, p + nxy);
+  else zp = (a.bc[5] == 0) ? u32(u, p - (long long)(a.nz - 1) * nxy) : ghost_or(a.bc[5], c);
+  const df lap = second_difference(xm, c, xp) * df{a.ix2[0], a.ix2[1]} +
+                 second_difference(ym, c, yp) * df{a.iy2[0], a.iy2[1]} +
+                 second_difference(zm, c, zp) * df{a.iz2[0], a.iz2[1]};
+  const df r = df_from_double(__ldg(a.f + p)) - lap;
+  a.r[p] = df_to_f32(r);
+}
+
+// u = fl32(u0) + d (- shift, the mean of u0, when the problem is singular and the result must be
+// mean-free); d is FP32, the sum is formed in double-float and rounded once to FP64.
+__global__ void __launch_bounds__(256) k_add(double* u, const float* d, long long n, const float2* shift) {
   long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
-  df v = df_from_double(u[p]) + df_from_double(__ldg(d + p));
+  df v;
+  two_sum(f32_from_double(u[p]), __ldg(d + p), v.hi, v.lo);
   if (shift) v = v - df{shift->x, shift->y};
   u[p] = df_to_double(v);
 }
@@ -100,14 +126,16 @@ static void split_h(double v, float* o) {
 
 cudaError_t launch_residual(const pp_plan* p, const void* f, const void* u, void* r, cudaStream_t st) {
   ResArgs a;
-  a.f = (const double*)f; a.u = (const double*)u; a.r = (double*)r;
+  a.f = (const double*)f; a.u = (const double*)u; a.r = (float*)r;
   a.nx = p->nx; a.ny = p->ny; a.nz = p->nz;
   for (int i = 0; i < 6; i++) a.bc[i] = p->bc[i];
   split_h(1.0 / (p->dx * p->dx), a.ix2);
   split_h(1.0 / (p->dy * p->dy), a.iy2);
   split_h(1.0 / (p->dz * p->dz), a.iz2);
-  long long n = (long long)p->nx * p->ny * p->nz;
-  k_residual<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a);
+  a.fd_ny = FastDiv::make((unsigned)p->ny);
+  const int threads = p->nx >= 256 ? 256 : (p->nx + 31) / 32 * 32;
+  const dim3 grid((unsigned)((long long)p->ny * p->nz), (unsigned)((p->nx + threads - 1) / threads));
+  k_residual<<<grid, threads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -176,7 +204,7 @@ cudaError_t launch_fill(void* x, long long n, bool f32, cudaStream_t st) {
 
 cudaError_t launch_add(const pp_plan* p, void* u, const void* d, const void* shift, cudaStream_t st) {
   long long n = (long long)p->nx * p->ny * p->nz;
-  k_add<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((double*)u, (const double*)d, n, (const float2*)shift);
+  k_add<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((double*)u, (const float*)d, n, (const float2*)shift);
   return cudaGetLastError();
 }
 

@@ -1,6 +1,6 @@
 // pp_noalloc.cu -- the refined mixed-precision solve without any device allocation.
 //
-// pp_solve_refined() allocates, on its first call on a plan, a grid-sized FP64 buffer for the
+// pp_solve_refined() allocates, on its first call on a plan, a grid-sized buffer for the
 // residual / correction and a small buffer for the partial sums of the mean.  Some callers
 // cannot allocate at that point: code that runs while a stream is being captured into a CUDA
 // graph (cudaMalloc is not a stream operation and is refused in that mode), time-stepping
@@ -16,8 +16,9 @@
 
 namespace {
 
-constexpr size_t kResidBytes = 16u << 20;                        // FP64 residual / correction
-constexpr long long kMaxPoints = (long long)(kResidBytes / sizeof(double));  // 2,097,152 cells
+constexpr size_t kResidBytes = 16u << 20;                        // residual / correction (FP32)
+constexpr long long kMaxPoints = 2097152;                        // cells (8 MiB of the 16 MiB in use)
+static_assert((size_t)kMaxPoints * sizeof(float) <= kResidBytes, "the residual of the largest grid fits");
 constexpr size_t kMeanBytes = (pp::kMeanParts + 1) * sizeof(float2);        // partial sums + mean
 constexpr size_t kScratchBytes = kResidBytes + kMeanBytes;
 
@@ -63,7 +64,7 @@ extern "C" pp_status pp_solve_refined_noalloc(pp_plan* p, const void* f, void* u
   if (npts > kMaxPoints) {
     char msg[200];
     snprintf(msg, sizeof msg,
-             "pp_solve_refined_noalloc: grid of %lld cells exceeds its fixed scratch of %lld cells (16 MiB of FP64); "
+             "pp_solve_refined_noalloc: grid of %lld cells exceeds the %lld cells of its fixed scratch; "
              "use pp_solve_refined for larger grids",
              npts, kMaxPoints);
     return set_last_error(PP_ERR_UNSUPPORTED_SIZE, msg);
@@ -75,23 +76,7 @@ extern "C" pp_status pp_solve_refined_noalloc(pp_plan* p, const void* f, void* u
   void* resid = base;                                            // residual, then correction
   void* partials = static_cast<unsigned char*>(base) + kResidBytes;
   float2* mean = static_cast<float2*>(partials) + pp::kMeanParts;
-  cudaStream_t st = (cudaStream_t)stream;
-
-  // Every value read below is first written by this call (the residual by the residual kernel,
-  // each partial sum by its block, the mean by the finishing block), so nothing needs clearing.
-  s = pp_solve(p, f, u, stream);
-  if (s != PP_OK) return s;
-  cudaError_t e = pp::launch_residual(p, f, u, resid, st);
-  if (e != cudaSuccess) return set_last_error(PP_ERR_CUDA, cudaGetErrorString(e));
-  s = pp_solve(p, resid, resid, stream);
-  if (s != PP_OK) return s;
-  const void* shift = nullptr;
-  if (p->singular) {
-    e = pp::launch_mean(p, u, partials, pp::kMeanParts, mean, st);
-    if (e != cudaSuccess) return set_last_error(PP_ERR_CUDA, cudaGetErrorString(e));
-    shift = mean;
-  }
-  e = pp::launch_add(p, u, resid, shift, st);
-  if (e != cudaSuccess) return set_last_error(PP_ERR_CUDA, cudaGetErrorString(e));
-  return PP_OK;
+  // Every value read is first written by this call (the residual by the residual kernel, each
+  // partial sum by its block, the mean by the finishing block), so nothing needs clearing.
+  return pp::solve_refined_core(p, f, u, resid, partials, mean, (cudaStream_t)stream);
 }

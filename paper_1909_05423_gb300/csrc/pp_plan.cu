@@ -598,15 +598,20 @@ cudaError_t launch_zsolve(const pp_plan* p, void* data, int transpose, cudaStrea
   a.qtab = p->d_qtab;
   split2(p->zscale, a.scale);
   a.transpose = transpose;
+  a.rstat = p->d_status;
+  a.dmin = 0x1p-100f;
+  a.umax = (float)(0x1p124 / ((double)p->nx * (double)p->ny));
   return launch_zsolve_impl(a, p->dtype == PP_F64, p->bc[4] == PP_BC_PERIODIC, st);
 }
 }  // namespace pp
 
 // One stage of the pipeline; the line stages may be restricted to planes z0 .. z0+nzc-1 (nzc < 0:
 // all planes; f and u always point at plane 0).
+// io: storage of f and u (ST_F64 / ST_F32); -1 = the plan's I/O type.  An FP32-transform plan may
+// also run with FP32 I/O (the refinement step's correction solve).
 static pp_status run_stage(pp_plan* p, int stage, const void* f, void* u, int transpose, cudaStream_t st,
-                           int z0 = 0, int nzc = -1) {
-  int io = (p->dtype == PP_MIXED_F32IO) ? ST_F32 : ST_F64;
+                           int z0 = 0, int nzc = -1, int io = -1) {
+  if (io < 0) io = (p->dtype == PP_MIXED_F32IO) ? ST_F32 : ST_F64;
   cudaError_t e = cudaSuccess;
   static const char* names[] = {"x-forward", "y-forward", "z-solve", "y-inverse", "x-inverse"};
   switch (stage) {
@@ -621,13 +626,40 @@ static pp_status run_stage(pp_plan* p, int stage, const void* f, void* u, int tr
   return PP_OK;
 }
 
-static pp_status run_pipeline(pp_plan* p, const void* f, void* u, int transpose, cudaStream_t st) {
+static pp_status run_pipeline(pp_plan* p, const void* f, void* u, int transpose, cudaStream_t st, int io = -1) {
   for (int s = 0; s < 5; s++) {
-    pp_status r = run_stage(p, s, f, u, transpose, st);
+    pp_status r = run_stage(p, s, f, u, transpose, st, 0, -1, io);
     if (r != PP_OK) return r;
   }
   return PP_OK;
 }
+
+namespace pp {
+// The refined solve on caller-provided scratch (pp_solve_refined and pp_solve_refined_noalloc):
+// u0 = solve(f) into u (FP64; FP32-exact values), r = f - A fl32(u0) into resid (FP32), the
+// correction solve delta = solve(r) in place with FP32 I/O, u = u0 + delta (- mean u0 when
+// singular).  resid: nx*ny*nz floats; partials: kMeanParts float2; mean: one float2.
+pp_status solve_refined_core(pp_plan* p, const void* f, void* u, void* resid, void* partials, void* mean,
+                             cudaStream_t st) {
+  pp_status s = run_pipeline(p, f, u, 0, st);
+  if (s != PP_OK) return s;
+  cudaError_t e = launch_residual(p, f, u, resid, st);
+  if (e != cudaSuccess) return fail(PP_ERR_CUDA, "residual launch: %s", cudaGetErrorString(e));
+  s = run_pipeline(p, resid, resid, 0, st, ST_F32);
+  if (s != PP_OK) return s;
+  // A singular problem is solved for the mean-free u; the FP32 first solve leaves a constant offset
+  // that the refinement step cannot see (it lies in the null space), so it is removed explicitly.
+  const void* shift = nullptr;
+  if (p->singular) {
+    e = launch_mean(p, u, partials, kMeanParts, mean, st);
+    if (e != cudaSuccess) return fail(PP_ERR_CUDA, "mean launch: %s", cudaGetErrorString(e));
+    shift = mean;
+  }
+  e = launch_add(p, u, resid, shift, st);
+  if (e != cudaSuccess) return fail(PP_ERR_CUDA, "update launch: %s", cudaGetErrorString(e));
+  return PP_OK;
+}
+}  // namespace pp
 
 // ------------------------------------------------------------------ autotuner
 // Times candidate launch shapes of each of the four line kernels on scratch grids and keeps the
@@ -728,7 +760,10 @@ static pp_status autotune(pp_plan* p) {
     if (run_stage(p, stage, f, u, 0, st) != PP_OK) break;  // leave this stage's output for the next one
   }
   const float bx = std::max(bt[0], bt[3]), by = std::max(bt[1], bt[2]);
+  cudaStreamSynchronize(st);
   cleanup();
+  // the timing runs' status (scratch data) is not the caller's
+  cudaMemset(p->d_status, 0, sizeof(unsigned));
   if (bx >= 1e30f || by >= 1e30f) return fail(PP_ERR_CUDA, "autotune: no candidate launch shape ran");
   choose_shapes(p, &best);
   std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -846,13 +881,13 @@ pp_status pp_plan_create(pp_plan** out, int nx, int ny, int nz, const pp_bc bc[6
   p->buf_bytes = (size_t)std::max(p->xplane, p->splane) * nz * p->elem;
   cudaError_t e = cudaMalloc(&p->bufA, p->buf_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&p->bufB, p->buf_bytes);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&p->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p->d_status, 4 * sizeof(unsigned));
   if (e != cudaSuccess) {
     free_plan(p);
     return fail(PP_ERR_OUT_OF_MEMORY, "workspace allocation of 2 x %zu bytes failed: %s", p->buf_bytes,
                 cudaGetErrorString(e));
   }
-  cudaMemset(p->d_status, 0, sizeof(int));
+  cudaMemset(p->d_status, 0, 4 * sizeof(unsigned));
   if (opt && opt->autotune) {
     pp_status ts = autotune(p);
     if (ts != PP_OK) { free_plan(p); return ts; }
@@ -911,31 +946,13 @@ pp_status pp_solve_refined(pp_plan* p, const void* f, void* u, pp_stream_t strea
   if (!p || !f || !u) return fail(PP_ERR_INVALID_ARG, "NULL plan or pointer");
   if (p->dtype != PP_MIXED_F64IO) return fail(PP_ERR_INVALID_ARG, "refinement needs a PP_MIXED_F64IO plan");
   if (f == u) return fail(PP_ERR_INVALID_ARG, "u must not alias f for the refined solve");
-  cudaStream_t st = (cudaStream_t)stream;
   if (!p->d_resid) {
-    size_t bytes = (size_t)p->nx * p->ny * p->nz * sizeof(double);
+    size_t bytes = (size_t)p->nx * p->ny * p->nz * sizeof(float);
     cudaError_t e = cudaMalloc(&p->d_resid, bytes);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_mean, (kMeanParts + 1) * sizeof(float2));
     if (e != cudaSuccess) return fail(PP_ERR_OUT_OF_MEMORY, "residual buffer (%zu bytes): %s", bytes, cudaGetErrorString(e));
   }
-  pp_status s = run_pipeline(p, f, u, 0, st);
-  if (s != PP_OK) return s;
-  cudaError_t e = launch_residual(p, f, u, p->d_resid, st);
-  if (e != cudaSuccess) return fail(PP_ERR_CUDA, "residual launch: %s", cudaGetErrorString(e));
-  s = run_pipeline(p, p->d_resid, p->d_resid, 0, st);
-  if (s != PP_OK) return s;
-  // A singular problem is solved for the mean-free u; the FP32 first solve leaves a constant offset
-  // that the refinement step cannot see (it lies in the null space), so it is removed explicitly.
-  const void* shift = nullptr;
-  if (p->singular) {
-    float2* mean = (float2*)p->d_mean + kMeanParts;
-    e = launch_mean(p, u, p->d_mean, kMeanParts, mean, st);
-    if (e != cudaSuccess) return fail(PP_ERR_CUDA, "mean launch: %s", cudaGetErrorString(e));
-    shift = mean;
-  }
-  e = launch_add(p, u, p->d_resid, shift, st);
-  if (e != cudaSuccess) return fail(PP_ERR_CUDA, "update launch: %s", cudaGetErrorString(e));
-  return PP_OK;
+  return solve_refined_core(p, f, u, p->d_resid, p->d_mean, (float2*)p->d_mean + kMeanParts, (cudaStream_t)stream);
 }
 
 pp_status pp_solve_batched(pp_plan* const* plans, const void* const* f, void* const* u, int n, pp_stream_t stream) {
@@ -1096,10 +1113,15 @@ pp_status pp_run_stage(pp_plan* p, int stage, const void* f, void* u, pp_stream_
 
 pp_status pp_plan_status(pp_plan* p) {
   if (!p) return fail(PP_ERR_INVALID_ARG, "NULL plan");
-  int v = 0;
-  CUDA_OK(cudaMemcpy(&v, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
-  CUDA_OK(cudaMemset(p->d_status, 0, sizeof(int)));
-  if (v) return fail((pp_status)v, "device reported status %d", v);
+  unsigned v = 0;
+  CUDA_OK(cudaMemcpy(&v, p->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  CUDA_OK(cudaMemset(p->d_status, 0, sizeof(unsigned)));
+  if (v & kStatusRange)
+    return fail(PP_ERR_RANGE,
+                "a solve met values outside the range of full accuracy: largest scaled z input below 2^-100, "
+                "largest z output above 2^124/(nx ny) = %.3g, or non-finite values; scale f by a power of two",
+                0x1p124 / ((double)p->nx * (double)p->ny));
+  if (v) return fail(PP_ERR_INTERNAL, "device reported status bits 0x%x", v);
   return PP_OK;
 }
 

@@ -27,9 +27,58 @@
 // source mean, pins u_0 = 0, solves rows 1..n-1, and shifts the result to zero mean.
 //
 // All arithmetic is double-float (pp_arith.cuh), whatever the storage type of the spill.
+//
+// Range report: the spill and the double-float pairs have FP32's exponent range.  Every thread
+// keeps the largest |value| of the scaled right-hand sides it reads and of the solutions it
+// writes; the blocks reduce them into two plan-owned words, and the last block of the launch
+// sets the plan's range bit when the largest scaled input lies below 2^-100 (then the low parts,
+// 2^-24 below, are subnormal and the solve loses accuracy norm-wise), or the largest output is
+// above 2^124 / (nx ny) (the inverse transforms, which sum up to 2 nx and 2 ny values, may
+// overflow), or a value is not finite.  The decision is per launch, on the largest magnitudes,
+// so tiny values beside large ones (the tails of a Gaussian source) never raise it.
 #include "pp_internal.h"
 
 namespace pp {
+
+// m = max(m, |v|) propagating NaN (max.NaN), one FMNMX per tracked value
+__device__ __forceinline__ void track(float& m, float v) {
+  asm("max.NaN.f32 %0, %0, %1;" : "+f"(m) : "f"(fabsf(v)));
+}
+__device__ __forceinline__ float max_nan(float a, float b) {
+  float r;
+  asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
+
+// Block reduction of the two maxima and the per-launch decision of the last block (256 threads).
+__device__ __forceinline__ void z_range_report(const ZArgs& a, float dmax, float umax) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dmax = max_nan(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    umax = max_nan(umax, __shfl_xor_sync(0xffffffffu, umax, o));
+  }
+  __shared__ float s_d[8], s_u[8];
+  const int w = (int)threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { s_d[w] = dmax; s_u[w] = umax; }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  float D = s_d[0], U = s_u[0];
+  for (int i = 1; i < ((int)blockDim.x + 31) / 32; i++) { D = max_nan(D, s_d[i]); U = max_nan(U, s_u[i]); }
+  // non-negative floats and NaN order as their bit patterns (sign cleared)
+  const unsigned db = __float_as_uint(D) & 0x7fffffffu, ub = __float_as_uint(U) & 0x7fffffffu;
+  unsigned* r = a.rstat;
+  if (db > *reinterpret_cast<volatile unsigned*>(r + 1)) atomicMax(r + 1, db);
+  if (ub > *reinterpret_cast<volatile unsigned*>(r + 2)) atomicMax(r + 2, ub);
+  __threadfence();
+  if (atomicAdd(r + 3, 1u) == gridDim.x - 1) {
+    // last block: every other block fenced its maxima before counting itself
+    __threadfence();
+    const float Dt = __uint_as_float(atomicExch(r + 1, 0u)), Ut = __uint_as_float(atomicExch(r + 2, 0u));
+    atomicExch(r + 3, 0u);
+    const bool bad = !(Dt <= 3.4e38f) || !(Ut <= a.umax) || (Dt > 0.0f && Dt < a.dmin);  // NaN fails <=
+    if (bad) atomicOr(r, kStatusRange);
+  }
+}
 
 // raw spill value -> double-float, and back
 __device__ __forceinline__ df zcvt(float2 v) { return df{v.x, v.y}; }
@@ -57,7 +106,8 @@ __device__ __forceinline__ void zload(S* v, const S* base, long long P, int k0, 
 
 // The singular mode: remove the source mean, pin u_0 = 0, solve rows 1..n-1, shift to zero mean.
 template <class S>
-__device__ __noinline__ void z_singular(S* base, long long P, int n, df scale, const float2* wt) {
+__device__ __noinline__ void z_singular(S* base, long long P, int n, df scale, const float2* wt, float& dmax,
+                                        float& umax) {
   df sum = df{0.f, 0.f};
   for (int k = 0; k < n; k++) sum = sum + zcvt(base[k * P]);
   df mean = sum * df_rcp(df{(float)n, 0.f});
@@ -65,6 +115,7 @@ __device__ __noinline__ void z_singular(S* base, long long P, int n, df scale, c
   df g = df{0.f, 0.f};
   for (int k = 1; k < n; k++) {
     df d = (zcvt(base[k * P]) - mean) * scale;
+    track(dmax, d.hi);
     g = (d - g) * f2df(__ldg(wt + (k - 1)));
     zput(base + k * P, g);
   }
@@ -78,7 +129,12 @@ __device__ __noinline__ void z_singular(S* base, long long P, int n, df scale, c
   }
   df umean = usum * df_rcp(df{(float)n, 0.f});
   zput(base, -umean);
-  for (int k = 1; k < n; k++) zput(base + k * P, zcvt(base[k * P]) - umean);
+  track(umax, umean.hi);
+  for (int k = 1; k < n; k++) {
+    const df v = zcvt(base[k * P]) - umean;
+    track(umax, v.hi);
+    zput(base + k * P, v);
+  }
 }
 
 // MODE 0: Thomas; 1: periodic z (Sherman-Morrison); 2: transposed factorisation (adjoint).
@@ -95,7 +151,7 @@ template <class S, int MODE> struct ZMinBlocks {
 };
 
 template <class S, int MODE>
-__global__ void __launch_bounds__(256, (ZMinBlocks<S, MODE>::v)) k_zsolve(const ZArgs a) {
+__device__ __forceinline__ void z_line(const ZArgs& a, float& dmax, float& umax) {
   long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= a.nreal) return;
   // slot s of the (padded) spectral plane -> row, column; padding columns carry no mode
@@ -111,7 +167,7 @@ __global__ void __launch_bounds__(256, (ZMinBlocks<S, MODE>::v)) k_zsolve(const 
   const float2* wt = a.wtab + m.woff;
   const int flags = m.flags;
   if (flags & ZF_SINGULAR) {
-    z_singular<S>(base, P, n, scale, wt);
+    z_singular<S>(base, P, n, scale, wt, dmax, umax);
     return;
   }
   const df winf = f2df(m.winf), wlast = f2df(m.wlast);
@@ -137,7 +193,9 @@ __global__ void __launch_bounds__(256, (ZMinBlocks<S, MODE>::v)) k_zsolve(const 
       if (ZFast<S, MODE>::v && k0 >= wlen && k0 >= qlen && k0 + ZU < n) {
 #pragma unroll
         for (int u = 0; u < ZU; u++) {
-          g = (zcvt(cur[u]) * scale - g) * winf;
+          const df d = zcvt(cur[u]) * scale;
+          track(dmax, d.hi);
+          g = (d - g) * winf;
           zput(base + (k0 + u) * P, g);
         }
       } else {
@@ -146,6 +204,7 @@ __global__ void __launch_bounds__(256, (ZMinBlocks<S, MODE>::v)) k_zsolve(const 
           const int k = k0 + u;
           if (k < n) {
             df d = zcvt(cur[u]) * scale;
+            track(dmax, d.hi);
             g = (d - g) * W(k);
             if (periodic && k < qlen) y0 = y0 + f2df(__ldg(qt + k)) * d;
             zput(base + k * P, g);
@@ -169,6 +228,7 @@ __global__ void __launch_bounds__(256, (ZMinBlocks<S, MODE>::v)) k_zsolve(const 
 #pragma unroll
         for (int t = 0; t < ZU; t++) {
           u = zcvt(cur[t]) - winf * u;
+          track(umax, u.hi);
           zput(base + (k0 - t) * P, u);
         }
 #pragma unroll
@@ -184,6 +244,7 @@ __global__ void __launch_bounds__(256, (ZMinBlocks<S, MODE>::v)) k_zsolve(const 
           else u = gk - W(k) * u;
           df outv = u;
           if (periodic && k < qlen) outv = u - cg * f2df(__ldg(qt + k));
+          track(umax, outv.hi);
           zput(base + k * P, outv);
         }
       }
@@ -202,6 +263,7 @@ __global__ void __launch_bounds__(256, (ZMinBlocks<S, MODE>::v)) k_zsolve(const 
         const int k = k0 + u;
         if (k < n) {
           df d = zcvt(cur[u]) * scale;
+          track(dmax, d.hi);
           h = (k == 0) ? d : d - wprev * h;
           wprev = W(k);
           zput(base + k * P, h);
@@ -220,6 +282,7 @@ __global__ void __launch_bounds__(256, (ZMinBlocks<S, MODE>::v)) k_zsolve(const 
         if (k >= 0) {
           const df hk = zcvt(cur[t]);
           x = (k == n - 1) ? hk * W(k) : (hk - x) * W(k);
+          track(umax, x.hi);
           zput(base + k * P, x);
         }
       }
@@ -227,6 +290,13 @@ __global__ void __launch_bounds__(256, (ZMinBlocks<S, MODE>::v)) k_zsolve(const 
       for (int t = 0; t < ZU; t++) cur[t] = nxt[t];
     }
   }
+}
+
+template <class S, int MODE>
+__global__ void __launch_bounds__(256, (ZMinBlocks<S, MODE>::v)) k_zsolve(const ZArgs a) {
+  float dmax = 0.0f, umax = 0.0f;
+  z_line<S, MODE>(a, dmax, umax);
+  z_range_report(a, dmax, umax);
 }
 
 template <class S>

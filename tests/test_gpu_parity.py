@@ -110,6 +110,27 @@ def test_periodic_z_long_lines(oracle, shape, bc):
     assert rel_l2(gpu_solve(f, bc, sp, "mixed_f64io"), ref) <= 1e-6
 
 
+@pytest.mark.parametrize("shape", [(1024, 8, 16), (768, 12, 10), (2048, 4, 6)])
+@pytest.mark.parametrize("bc", ["NNDDNN", "NNNNDD", "DNDNND"])
+def test_thomas_z_long_lines(oracle, shape, bc):
+    """Long non-periodic z lines on a random source, element by element against the oracle.  The
+    low (kx, ky) modes are the weakly dominant ones: their Thomas multipliers approach the fixed
+    point slowly, so the stored prefix is long and the switch to the converged multiplier (and, in
+    the FP32-spill sweeps, the converged-batch fast path) is exercised far into the line."""
+    nz, ny, nx = shape
+    sp = (1.0 / nx, 1.0 / ny, 1.0 / nz)
+    f = workloads.uniform_source(shape, seed=17, remove_mean=False)
+    ref = oracle.solve(f, bc, sp)
+    assert rel_l2(gpu_solve(f, bc, sp), ref) <= TOL_F64
+    assert rel_l2(gpu_solve(f, bc, sp, "mixed_f64io"), ref) <= 1e-6
+    assert rel_l2(gpu_solve(f, bc, sp, "mixed_f32io"), ref) <= 1e-6
+    # a z-only source puts all of its energy into the (0,0)-neighbourhood modes, the slowest to converge
+    fz = np.broadcast_to(np.random.default_rng(18).uniform(-1, 1, size=(nz, 1, 1)), shape).copy()
+    fz[:, 0, 0] += 0.25
+    refz = oracle.solve(fz, bc, sp)
+    assert rel_l2(gpu_solve(fz, bc, sp), refz) <= TOL_F64
+
+
 def test_singular_zero_mean(oracle):
     shape = (16, 24, 36)
     rng = np.random.default_rng(5)
