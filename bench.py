@@ -62,7 +62,8 @@ KERNEL_SOURCES = ("pp_arith.cuh", "pp_fft.cuh", "pp_internal.h", "pp_lines.cuh",
                   "pp_lines_f32_tiny.cu", "pp_lines_df_small.cu",
                   "pp_lines_df_large.cu", "pp_lines_df_any.cu", "pp_lines_df_any57.cu", "pp_lines_f32_small.cu",
                   "pp_lines_f32_large.cu", "pp_lines_f32_any.cu", "pp_lines_f32_any57.cu", "pp_lines_df_ct3a.cu",
-                  "pp_lines_df_ct3b.cu", "pp_lines_f32_ct3a.cu", "pp_lines_f32_ct3b.cu", "pp_zsolve.cu", "pp_misc.cu")
+                  "pp_lines_df_ct3b.cu", "pp_lines_f32_ct3a.cu", "pp_lines_f32_ct3b.cu", "pp_zsolve.cu", "pp_misc.cu",
+                  "pp_zfft.cu", "pp_range.cuh")
 
 
 def _code_only(text: str) -> str:
@@ -257,15 +258,15 @@ def _events_ms(fn, reps, warmup=2):
 
 
 def _config3(pp, workloads, args):
-    """512^3 mixed precision (FP32 transforms, double-float z, one FP64 refinement step), all-periodic
-    and all-Neumann manufactured cos/sin products; errors against the exact discrete solution (which the
-    FP64 oracle reproduces to roundoff) and the FP64 path; rates with and without refinement."""
+    """Mixed precision (FP32 transforms, double-float z) with and without one refinement step, and the
+    FP64-class path, at 512^3 and 1024^3: all-periodic and all-Neumann manufactured cos/sin products
+    (built on the device).  Errors against the exact discrete solution -- each product term is a
+    discrete eigenvector, u = u* sum(k^2) / sum(lambda_d), with lambda_d = -4 sin^2(k h / 2) / h^2
+    (the cancellation-free form) -- and rates.  The all-periodic case also times periodic z by
+    transform (z_method 2) against Sherman-Morrison (z_method 1)."""
     import math
 
-    import numpy as np
     import torch
-    n = args.n3
-    sp = (1.0 / n,) * 3
     out = {}
     cases = {
         "PPPPPP": [(1.0, ("cos", 2 * math.pi), ("cos", 2 * math.pi), ("cos", 2 * math.pi)),
@@ -273,40 +274,77 @@ def _config3(pp, workloads, args):
         "NNNNNN": [(1.0, ("cos", math.pi), ("cos", 3 * math.pi), ("cos", 6 * math.pi)),
                    (0.5, ("cos", 2 * math.pi), ("cos", math.pi), ("cos", 2 * math.pi))],
     }
-    h = 1.0 / n
-    lam = lambda k: (2.0 * math.cos(k * h) - 2.0) / (h * h)
-    for bc, terms in cases.items():
-        u_star, f = workloads.manufactured((n, n, n), sp, terms)
-        # exact discrete solution: each product term is a discrete eigenvector
-        u_dis = np.zeros_like(u_star)
-        for amp, (fx, kx), (fy, ky), (fz, kz) in terms:
-            t, _ = workloads.manufactured((n, n, n), sp, [(amp, (fx, kx), (fy, ky), (fz, kz))])
-            u_dis += t * (-(kx * kx + ky * ky + kz * kz) / (lam(kx) + lam(ky) + lam(kz)))
-        u_dis -= u_dis.mean()
-        ft = torch.from_numpy(f).cuda()
-        ref = torch.from_numpy(u_dis).cuda()
-        p64 = pp.Plan((n, n, n), bc, sp, "f64")
-        pm = pp.Plan((n, n, n), bc, sp, "mixed_f64io")
-        u64, um, ur = torch.empty_like(ft), torch.empty_like(ft), torch.empty_like(ft)
-        t64 = _events_ms(lambda: p64.solve(ft, u64), args.steps)
-        tm = _events_ms(lambda: pm.solve(ft, um), args.steps)
-        tr = _events_ms(lambda: pm.solve_refined(ft, ur), args.steps)
-        nrm = torch.linalg.vector_norm(ref).item()
-        rel = lambda x: torch.linalg.vector_norm(x - ref).item() / nrm
-        out[bc] = {"n": n, "f64_ms": t64, "mixed_ms": tm, "refined_ms": tr,
-                   "f64_gpoints_s": n ** 3 / t64 / 1e6, "mixed_gpoints_s": n ** 3 / tm / 1e6,
-                   "refined_gpoints_s": n ** 3 / tr / 1e6, "mixed_speedup_vs_f64": t64 / tm,
-                   "rel_l2_vs_exact_discrete": {"f64": rel(u64), "mixed": rel(um), "refined": rel(ur)}}
-        p64.close()
-        pm.close()
-        del ft, ref, u64, um, ur
-        torch.cuda.empty_cache()
+    tune = {} if args.no_autotune else {"autotune": 1}
+    for n in args.n3:
+        sp = (1.0 / n,) * 3
+        h = 1.0 / n
+        lam = lambda k: -4.0 * math.sin(0.5 * k * h) ** 2 / (h * h)
+        for bc, terms in cases.items():
+            ref = torch.zeros((n, n, n), dtype=torch.float64, device="cuda")
+            ft = torch.zeros_like(ref)
+            for amp, (fx, kx), (fy, ky), (fz, kz) in terms:
+                t, ff = workloads.manufactured_device((n, n, n), sp, [(amp, (fx, kx), (fy, ky), (fz, kz))])
+                ref += t * (-(kx * kx + ky * ky + kz * kz) / (lam(kx) + lam(ky) + lam(kz)))
+                ft += ff
+                del t, ff
+            ref -= ref.mean()
+            nrm = torch.linalg.vector_norm(ref).item()
+            rel = lambda x: torch.linalg.vector_norm(x - ref).item() / nrm
+            u = torch.empty_like(ft)
+            res = {"n": n}
+            zm = [1, 2] if bc[4] == "P" else [0]
+            for z in zm:
+                tag = "" if z != 2 else "_ztransform"
+                opts = dict(tune, z_method=z)
+                p64 = pp.Plan((n, n, n), bc, sp, "f64", options=opts)
+                t64 = _events_ms(lambda: p64.solve(ft, u), args.steps)
+                res["f64%s_ms" % tag] = t64
+                res["f64%s_gpoints_s" % tag] = n ** 3 / t64 / 1e6
+                res["rel_l2_f64%s" % tag] = rel(u)
+                p64.close()
+                pm = pp.Plan((n, n, n), bc, sp, "mixed_f64io", options=opts)
+                tm = _events_ms(lambda: pm.solve(ft, u), args.steps)
+                res["mixed%s_ms" % tag] = tm
+                res["mixed%s_gpoints_s" % tag] = n ** 3 / tm / 1e6
+                res["rel_l2_mixed%s" % tag] = rel(u)
+                if z != 2:
+                    tr = _events_ms(lambda: pm.solve_refined(ft, u), args.steps)
+                    res["refined_ms"] = tr
+                    res["refined_gpoints_s"] = n ** 3 / tr / 1e6
+                    res["rel_l2_refined"] = rel(u)
+                    res["mixed_speedup_vs_f64"] = t64 / tm
+                pm.close()
+            out["%s_%d" % (bc, n)] = res
+            del ft, ref, u
+            torch.cuda.empty_cache()
+    return out
+
+
+def _config2_256(pp, args):
+    """The headline workload (Neumann-x / Dirichlet-y / Neumann-z, U[-1,1] source, mean removed) at
+    256^3: grids of 128 MiB, about the size of L2, so the HBM fraction is not the target there."""
+    import torch
+    n = 256
+    shape = (n, n, n)
+    sp = (1.0 / n,) * 3
+    g = torch.Generator(device="cuda")
+    g.manual_seed(SEED)
+    f = torch.empty(shape, dtype=torch.float64, device="cuda").uniform_(-1.0, 1.0, generator=g)
+    f -= f.mean()
+    u = torch.empty_like(f)
+    tune = {} if args.no_autotune else {"autotune": 1}
+    out = {"n": n}
+    for dtype in ("f64", "mixed_f64io"):
+        plan = pp.Plan(shape, BC, sp, dtype, options=tune)
+        ms = _events_ms(lambda: plan.solve(f, u), max(args.steps, 20))
+        out[dtype] = {"ms": ms, "gpoints_s": n ** 3 / ms / 1e6}
+        plan.close()
     return out
 
 
 def _config4(pp, workloads, args):
     """64 independent grids, sides drawn from {32,...,256} per axis and boundary conditions per axis/face,
-    U[-1,1] sources; one graph launch per batch (FP64 and FP32 I/O)."""
+    U[-1,1] sources; one graph launch per batch (FP64 and FP32 I/O); every plan autotuned."""
     import torch
     grids = workloads.batched_grids(seed=4, count=64)
     pts = sum(s[0] * s[1] * s[2] for s, _ in grids)
@@ -314,7 +352,8 @@ def _config4(pp, workloads, args):
     g = torch.Generator(device="cuda")
     g.manual_seed(4)
     for dtype, tdt in (("f64", torch.float64), ("mixed_f32io", torch.float32)):
-        plans = [pp.Plan(s, bc, (1.0 / s[2], 1.0 / s[1], 1.0 / s[0]), dtype) for s, bc in grids]
+        tune = {} if args.no_autotune else {"autotune": 1}
+        plans = [pp.Plan(s, bc, (1.0 / s[2], 1.0 / s[1], 1.0 / s[0]), dtype, options=tune) for s, bc in grids]
         fs = [torch.empty(s, dtype=tdt, device="cuda").uniform_(-1.0, 1.0, generator=g) for s, _ in grids]
         us = [torch.empty_like(x) for x in fs]
         ms = _events_ms(lambda: pp.solve_batched(plans, fs, us), args.steps)
@@ -347,6 +386,88 @@ def _config5(pp, workloads, args):
     ms = _events_ms(step, args.steps)
     plan.close()
     return {"n": n, "ms_forward_plus_adjoint": ms, "gpoints_s_forward_plus_adjoint": n ** 3 / ms / 1e6}
+
+
+def _copy_gbs(fh, uh, dev):
+    """Plain pinned host<->device copy bandwidth of the e2e buffers (one whole-grid copy each way,
+    CUDA events on the current stream), GB/s."""
+    import torch
+    st = torch.cuda.current_stream()
+    out = []
+    for src, dst in ((fh, dev), (dev, uh)):
+        dst.copy_(src, non_blocking=True)  # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        dst.copy_(src, non_blocking=True)
+        e1.record(st)
+        torch.cuda.synchronize()
+        out.append(src.numel() * src.element_size() / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+    return out[0], out[1]
+
+
+class HostPlacement:
+    """The GPU's CPU and NUMA affinity (nvidia-smi topo -m) and where the pinned pages live
+    (/proc/self/numa_maps).  bind() restricts this process to the GPU-local CPUs while the pinned
+    buffers are allocated and touched; unbind() restores the previous affinity."""
+
+    def __init__(self, index):
+        self.index = index
+        self.cpus, self.numa, self.saved = None, None, None
+        try:
+            txt = subprocess.run(["nvidia-smi", "topo", "-m"], capture_output=True, text=True, timeout=20).stdout
+            lines = [ln for ln in txt.splitlines() if ln.strip()]
+            head = lines[0].split("\t")
+            row = next(ln for ln in lines[1:] if ln.split("\t")[0].strip() == "GPU%d" % index).split("\t")
+            cols = {h.strip(): i for i, h in enumerate(head)}
+            # a header without an empty leading cell (for the row names) is shifted by one
+            sh = 0 if head[0].strip() == "" else 1
+            cpu_s = row[cols["CPU Affinity"] + sh].strip() if "CPU Affinity" in cols else ""
+            self.numa = row[cols["NUMA Affinity"] + sh].strip() if "NUMA Affinity" in cols else None
+            cpus = set()
+            for part in cpu_s.split(","):
+                if "-" in part:
+                    lo, hi = part.split("-")
+                    cpus.update(range(int(lo), int(hi) + 1))
+                elif part.strip().isdigit():
+                    cpus.add(int(part))
+            self.cpus = sorted(cpus & os.sched_getaffinity(0)) or None
+        except Exception:
+            pass
+
+    def bind(self):
+        try:
+            self.saved = os.sched_getaffinity(0)
+            if self.cpus:
+                os.sched_setaffinity(0, self.cpus)
+        except Exception:
+            self.saved = None
+
+    def unbind(self):
+        if self.saved:
+            try:
+                os.sched_setaffinity(0, self.saved)
+            except Exception:
+                pass
+
+    @staticmethod
+    def _pages(addr):
+        """N<node>=pages of the mapping that holds addr."""
+        try:
+            best = None
+            with open("/proc/self/numa_maps") as fh:
+                for ln in fh:
+                    start = int(ln.split()[0], 16)
+                    if start <= addr and (best is None or start > best[0]):
+                        best = (start, ln)
+            return {kv.split("=")[0]: int(kv.split("=")[1]) for kv in best[1].split() if kv[:1] == "N" and "=" in kv}
+        except Exception:
+            return None
+
+    def report(self, *addrs):
+        return {"gpu_cpu_affinity": (("%d-%d" % (self.cpus[0], self.cpus[-1])) if self.cpus else None),
+                "gpu_numa_affinity": self.numa, "bound_to_gpu_cpus": bool(self.cpus),
+                "pinned_pages_per_node": [self._pages(a) for a in addrs]}
 
 
 def run_ours(args):
@@ -453,18 +574,19 @@ def run_ours(args):
             d["alu_tops"] = opr * npts / (per[k] * 1e-3) / 1e12
             d["alu_frac"] = d["alu_tops"] / alu_peak
         per_stage[name] = d
+    # the roofline block is the dominant kernel's HBM fraction (algorithmic bytes of that launch over
+    # its CUDA-event time, against the measured copy bandwidth); the line kernels are in fact bound by
+    # FP32 instruction issue in double-float arithmetic, so that fraction is reported beside it
+    roof = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs, copy bandwidth)" % peak_kind,
+            "traffic": None if args.shape else _traffic(dname, n), "alg_bytes_per_launch": alg_bytes[dname],
+            "alg_bytes_per_point": alg_bytes[dname] / npts}
     if dname in kinds:
-        roof = {"bound": "alu", "kernel": dname, "achieved": per_stage[dname]["alu_tops"], "peak": alu_peak,
-                "unit": "TFLOP/s", "frac": per_stage[dname]["alu_frac"],
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz; FP32 operations counted as "
-                               "issued lane instructions (FMA = 1)",
-                "alg_fp32_ops_per_point": per_stage[dname]["fp32_ops_per_point"],
-                "hbm_frac": per_stage[dname]["hbm_frac"], "traffic": None if args.shape else _traffic(dname, n),
-                "alg_bytes_per_launch": alg_bytes[dname]}
-    else:
-        roof = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_kind, "traffic": None if args.shape else _traffic(dname, n),
-                "alg_bytes_per_launch": alg_bytes[dname]}
+        roof["alu"] = {"achieved": per_stage[dname]["alu_tops"], "peak": alu_peak,
+                       "unit": "T FP32 lane instructions/s", "frac": per_stage[dname]["alu_frac"],
+                       "alg_fp32_instr_per_point": per_stage[dname]["fp32_ops_per_point"],
+                       "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz; algorithmic double-float "
+                                      "operations counted as the FP32 lane instructions they issue (FMA = 1)"}
 
     # ---------------------------------------------------------------- mixed precision variants
     variants = {}
@@ -489,6 +611,7 @@ def run_ours(args):
     if not args.no_variants:
         del u
         torch.cuda.empty_cache()
+        variants["config2_256"] = _config2_256(pp, args)
         variants["config3_mixed_mms"] = _config3(pp, workloads, args)
         variants["config4_batched"] = _config4(pp, workloads, args)
         variants["config5_adjoint"] = _config5(pp, workloads, args)
@@ -498,9 +621,13 @@ def run_ours(args):
     # ---------------------------------------------------------------- end to end through host buffers
     e2e = None
     if not args.no_e2e:
+        host = HostPlacement(local)
+        host.bind()  # pinned buffers allocated (and first touched) by a thread on the GPU's own NUMA node
         fh = torch.empty(shape, dtype=torch.float64, pin_memory=True)
-        fh.copy_(f.cpu())
         uh = torch.empty(shape, dtype=torch.float64, pin_memory=True)
+        fh.copy_(f.cpu())
+        uh.zero_()
+        h2d, d2h = _copy_gbs(fh, uh, f)
         plan.solve_host(fh, uh)
         barrier()
         t0 = time.perf_counter()
@@ -508,7 +635,11 @@ def run_ours(args):
         for _ in range(ke):
             plan.solve_host(fh, uh)
         dt = (time.perf_counter() - t0) / ke
-        e2e = {"value": npts / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": npts * 8, "d2h_bytes_per_step": npts * 8}
+        e2e = {"value": npts / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": npts * 8, "d2h_bytes_per_step": npts * 8,
+               "ms_per_step": dt * 1e3, "h2d_gbs": h2d, "d2h_gbs": d2h,
+               "copy_floor_ms": npts * 8 / (h2d * 1e9) * 1e3 + npts * 8 / (d2h * 1e9) * 1e3,
+               "host": host.report(fh.data_ptr(), uh.data_ptr())}
+        host.unbind()
         del fh, uh
 
     cpu = None
@@ -561,7 +692,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="fixed launch-shape heuristics instead of the autotuner")
-    ap.add_argument("--n3", type=int, default=512, help="grid side of the config-3 mixed-precision variant")
+    ap.add_argument("--n3", type=int, nargs="+", default=[512, 1024],
+                    help="grid sides of the config-3 mixed-precision variant")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

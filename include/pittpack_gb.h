@@ -81,7 +81,11 @@ typedef struct pp_plan_options {
   int lines_x_inv;   /*   (0 = as the forward setting above)                      */
   int threads_y_inv;
   int cols_y_inv;
-  int reserved[3]; /* must be zero */
+  int z_method;    /* periodic z only: 0 = automatic (Sherman-Morrison, or with autotune = 1 the
+                      faster of the two, timed), 1 = Sherman-Morrison sweeps, 2 = DFT along z and a
+                      diagonal solve (needs nz = 2^a 3^b 5^c 7^d <= 4096, else
+                      PP_ERR_UNSUPPORTED_SIZE); ignored for non-periodic z */
+  int reserved[2]; /* must be zero */
 } pp_plan_options;
 
 typedef struct pp_plan pp_plan;
@@ -220,6 +224,11 @@ size_t pp_plan_device_bytes(const pp_plan* plan);
  * kernels, real lines: two per complex column when its parts are transformed separately).
  * Errors: PP_ERR_INVALID_ARG (NULL). */
 pp_status pp_plan_launch_shapes(const pp_plan* plan, int out[8]);
+
+/* How the plan solves along z: *out = 0 (non-periodic z: Thomas), 1 (periodic z: Sherman-Morrison
+ * sweeps) or 2 (periodic z: DFT along z and a diagonal solve), as chosen by options.z_method or the
+ * autotuner.  Errors: PP_ERR_INVALID_ARG (NULL). */
+pp_status pp_plan_z_method(const pp_plan* plan, int* out);
 
 /* Human-readable detail of the last error on the calling thread ("" if none). */
 const char* pp_last_error_string(void);

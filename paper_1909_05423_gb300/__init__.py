@@ -156,6 +156,12 @@ class Plan:
         names = ["x-forward", "y-forward", "y-inverse", "x-inverse"]
         return {k: (v[2 * i], v[2 * i + 1]) for i, k in enumerate(names)}
 
+    def z_method(self) -> str:
+        """How z is solved: "thomas" (non-periodic z), "sherman-morrison" or "transform" (periodic z)."""
+        v = ctypes.c_int()
+        _lib.check(_lib.load().pp_plan_z_method(self._h, ctypes.byref(v)))
+        return {0: "thomas", 1: "sherman-morrison", 2: "transform"}[v.value]
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             _lib.load().pp_plan_destroy(self._h)

@@ -110,6 +110,20 @@ struct ZArgs {
 // status bits of a plan's device status word
 constexpr unsigned kStatusRange = 1u;
 
+// Diagonal solve of periodic z by transform (pp_zfft.cu), in place on the z-transformed spectrum.
+struct ZDiagArgs {
+  void* data;          // spectral array [nz][plane] (spill type)
+  long long plane;     // reals per z-plane
+  long long nreal;     // reals per plane carrying lines (even: complex lines of real pairs)
+  int nz;
+  const float2* lam;   // per real slot: lambda_x/dx^2 + lambda_y/dy^2 of its mode (hi, lo)
+  const float2* zeig;  // per kz: (2 cos(2 pi kz/nz) - 2)/dz^2 (hi, lo)
+  float scale[2];      // w_x w_y / nz (hi, lo)
+  unsigned* rstat;     // range report (as ZArgs)
+  float dmin, umax;
+};
+enum { ZM_SM = 0, ZM_FFT = 1 };  // periodic z: Sherman-Morrison sweeps / z transform
+
 }  // namespace pp
 
 // Plan object behind the opaque C handle.
@@ -148,6 +162,14 @@ struct pp_plan {
   cudaStream_t host_cs[2];  // copy streams of host-buffer solves (created on first use)
   cudaEvent_t host_ev[2 * pp::kHostChunks + 3];  // per-chunk copy / compute events, start, two joins
   unsigned* d_status;  // 4 words: status bits, two running maxima and a block counter (ZArgs::rstat)
+  // periodic z by transform (zmethod == ZM_FFT): z-line DFT plan and twiddles, diagonal tables
+  int zmethod;
+  bool zfft_ok;         // periodic z with an nz the line kernels can transform
+  pp::FftPlan fz;
+  void* d_tw_z; void* d_aux_z;
+  float2* d_zlam;       // per real slot of a plane
+  float2* d_zeig;       // per kz
+  int threads_z, lpc_z, ldm_z;
 };
 
 namespace pp {
@@ -156,6 +178,8 @@ namespace pp {
 cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_out, const void* in, void* out,
                          cudaStream_t st, int z0 = 0, int nzc = -1);
 cudaError_t launch_zsolve(const pp_plan* p, void* data, int transpose, cudaStream_t st);
+// periodic z by transform: forward z DFT, diagonal solve, inverse z DFT (in place)
+cudaError_t launch_zfft(const pp_plan* p, void* data, cudaStream_t st);
 cudaError_t launch_residual(const pp_plan* p, const void* f, const void* u, void* r, cudaStream_t st);
 cudaError_t launch_add(const pp_plan* p, void* u, const void* d, const void* shift, cudaStream_t st);
 // f -= coef * g on the cells next to face `face` (0..5 = x-,x+,y-,y+,z-,z+), in place

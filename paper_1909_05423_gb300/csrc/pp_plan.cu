@@ -32,6 +32,7 @@ namespace pp {
 cudaError_t launch_lines_impl(const LineArgs& a, bool df_arith, int oy, int sin, int sout, int threads,
                               cudaStream_t st);
 cudaError_t launch_zsolve_impl(const ZArgs& a, bool df_spill, bool zper, cudaStream_t st);
+cudaError_t launch_zdiag_impl(const ZDiagArgs& a, bool df_spill, cudaStream_t st);
 }  // namespace pp
 
 using namespace pp;
@@ -360,10 +361,38 @@ static pp_status z_tables(pp_plan* p) {
   return upload((void**)&p->d_qtab, qtab);
 }
 
+// Tables of periodic z by transform: the z-line DFT (complex, length nz), the x/y eigenvalue sum of
+// the mode of every real slot of a spectral plane (padding slots: -1, never singular) and the z
+// eigenvalue per kz.  Same FP64 expressions as the tridiagonal tables.
+static pp_status zfft_tables(pp_plan* p) {
+  pp_status s = axis_tables(p, AX_P, p->nz, true, p->fz, &p->d_tw_z, &p->d_aux_z);
+  if (s != PP_OK) return s;
+  const int nx = p->nx, ny = p->ny;
+  long long row_reals, row_valid, rows;
+  bool cplx;
+  if (p->layout == 1) { row_reals = 2LL * nx; row_valid = 2LL * nx; rows = ny / 2 + 1; cplx = true; }
+  else if (p->layout == 0) { row_reals = p->xrow; row_valid = nx + 2; rows = ny; cplx = true; }
+  else { row_reals = p->xrow; row_valid = nx; rows = ny; cplx = false; }
+  std::vector<float> lam((size_t)(2 * p->splane));
+  for (long long r = 0; r < rows; r++) {
+    const double ly = axis_eig(p->ky, ny, (int)r) / (p->dy * p->dy);
+    for (long long c = 0; c < row_reals; c++) {
+      double v = -1.0;
+      if (c < row_valid) v = axis_eig(p->kx, nx, (int)(cplx ? c / 2 : c)) / (p->dx * p->dx) + ly;
+      split2(v, &lam[(size_t)(2 * (r * row_reals + c))]);
+    }
+  }
+  std::vector<float> eig((size_t)(2 * p->nz));
+  for (int k = 0; k < p->nz; k++) split2(axis_eig(AX_P, p->nz, k) / (p->dz * p->dz), &eig[(size_t)(2 * k)]);
+  if ((s = upload((void**)&p->d_zlam, lam)) != PP_OK) return s;
+  return upload((void**)&p->d_zeig, eig);
+}
+
 static void free_plan(pp_plan* p) {
   if (!p) return;
   void* ptrs[] = {p->bufA, p->bufB, p->d_tw_x, p->d_aux_x, p->d_tw_y, p->d_aux_y, p->d_modes, p->d_wtab,
-                  p->d_qtab, p->d_resid, p->d_mean, p->d_host_f, p->d_host_u, p->d_status};
+                  p->d_qtab, p->d_resid, p->d_mean, p->d_host_f, p->d_host_u, p->d_status,
+                  p->d_tw_z, p->d_aux_z, p->d_zlam, p->d_zeig};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (cudaStream_t s : p->host_cs)
@@ -456,6 +485,25 @@ static void choose_shapes(pp_plan* p, const pp_plan_options* opt) {
       p->lpc_y[dir] = cols * parts;
       p->ldm_y = ldm;
     }
+  }
+  // z lines of periodic z by transform: complex columns (one per real pair of a plane), the y
+  // kernels' heuristic with the z length
+  if (p->zfft_ok) {
+    const int M = p->fz.M;
+    const size_t col_bytes = 2 * se;
+    const int cpt = values_per_thread(p->fz, 1, p->dtype == PP_F64);
+    const int tmin = std::max(32, ((M + cpt - 1) / cpt + 31) / 32 * 32);
+    int T = 128;
+    while (T < 512 && (size_t)std::max(1, cpt * T / std::max(M, 1)) * col_bytes < 32) T *= 2;
+    T = std::max(T, tmin);
+    int cols = std::max(1, cpt * T / std::max(M, 1));
+    cols = std::min<long long>(std::min(cols, kMaxLpc), p->splane / 2);
+    const int ldm = M + (M >> 5) + 1;
+    auto need = [&](int c) { return (size_t)c * ldm * cs + (size_t)M * cs + 16 * (size_t)c; };
+    while (cols > 1 && need(cols) > smem_cap) cols--;
+    p->threads_z = T;
+    p->lpc_z = cols;
+    p->ldm_z = ldm;
   }
 }
 
@@ -603,6 +651,62 @@ cudaError_t launch_zsolve(const pp_plan* p, void* data, int transpose, cudaStrea
   a.umax = (float)(0x1p124 / ((double)p->nx * (double)p->ny));
   return launch_zsolve_impl(a, p->dtype == PP_F64, p->bc[4] == PP_BC_PERIODIC, st);
 }
+
+// z lines as strided columns: the y-orientation kernels with one "plane" of splane/2 complex columns
+// (adjacent columns 2 reals apart) and positions one z-plane apart; in place (a tile is read whole
+// before it is written)
+static cudaError_t launch_zlines(const pp_plan* p, int dir, void* data, cudaStream_t st) {
+  LineArgs a;
+  memset(&a, 0, sizeof a);
+  const bool dfm = (p->dtype == PP_F64);
+  const long long ncols = p->splane / 2;
+  a.N = p->nz;
+  a.kind = dir == 0 ? LK_C2C_F : LK_C2C_I;
+  a.parts = 1;
+  a.lines_per_plane = (int)ncols;
+  a.nlines = (int)ncols;
+  a.lpc = p->lpc_z;
+  a.ldm = p->ldm_z;
+  a.fp = p->fz;
+  a.tw = p->d_tw_z;
+  a.aux = p->d_aux_z;
+  a.in_plane = 0; a.out_plane = 0;
+  a.in_line = 2; a.out_line = 2;
+  a.in_pos = (int)p->splane; a.out_pos = p->splane;
+  a.in = data;
+  a.out = data;
+  if ((long long)a.lpc * a.fp.M > (long long)values_per_thread(a.fp, 1, dfm) * p->threads_z)
+    return cudaErrorInvalidConfiguration;
+  a.tx = a.lpc;
+  a.ncols = (int)ncols;
+  a.nblk = (int)((ncols + a.tx - 1) / a.tx);
+  a.ntiles = a.nblk;
+  a.vec_y = 0;
+  a.fd_gpc = FastDiv::make(1u);
+  finish_args(a);
+  a.fd_nblk = FastDiv::make((unsigned)a.nblk);
+  return launch_lines_impl(a, dfm, 1, ST_SPILL, ST_SPILL, p->threads_z, st);
+}
+
+cudaError_t launch_zfft(const pp_plan* p, void* data, cudaStream_t st) {
+  cudaError_t e = launch_zlines(p, 0, data, st);
+  if (e != cudaSuccess) return e;
+  ZDiagArgs d;
+  memset(&d, 0, sizeof d);
+  d.data = data;
+  d.plane = p->splane;
+  d.nreal = p->splane;
+  d.nz = p->nz;
+  d.lam = p->d_zlam;
+  d.zeig = p->d_zeig;
+  split2(axis_weight(p->kx, p->nx) * axis_weight(p->ky, p->ny) / p->nz, d.scale);
+  d.rstat = p->d_status;
+  d.dmin = 0x1p-100f;
+  d.umax = (float)(0x1p124 / ((double)p->nx * (double)p->ny * (double)p->nz));
+  e = launch_zdiag_impl(d, p->dtype == PP_F64, st);
+  if (e != cudaSuccess) return e;
+  return launch_zlines(p, 1, data, st);
+}
 }  // namespace pp
 
 // One stage of the pipeline; the line stages may be restricted to planes z0 .. z0+nzc-1 (nzc < 0:
@@ -617,7 +721,10 @@ static pp_status run_stage(pp_plan* p, int stage, const void* f, void* u, int tr
   switch (stage) {
     case 0: e = launch_lines(p, 0, 0, io, ST_SPILL, f, p->bufA, st, z0, nzc); break;
     case 1: e = launch_lines(p, 1, 0, ST_SPILL, ST_SPILL, p->bufA, p->bufB, st, z0, nzc); break;
-    case 2: e = launch_zsolve(p, p->bufB, transpose, st); break;
+    case 2:
+      // periodic z by transform is self-adjoint (the z eigenvalues are even in kz)
+      e = (p->zmethod == ZM_FFT) ? launch_zfft(p, p->bufB, st) : launch_zsolve(p, p->bufB, transpose, st);
+      break;
     case 3: e = launch_lines(p, 1, 1, ST_SPILL, ST_SPILL, p->bufB, p->bufA, st, z0, nzc); break;
     case 4: e = launch_lines(p, 0, 1, ST_SPILL, io, p->bufA, u, st, z0, nzc); break;
     default: return fail(PP_ERR_INVALID_ARG, "stage %d out of range", stage);
@@ -669,12 +776,13 @@ namespace {
 struct TuneEnt {
   int dev, nx, ny, nz, dtype, bc[6];
   pp_plan_options best;
+  int zmethod;
 };
 std::mutex g_tune_mu;
 std::vector<TuneEnt> g_tune_cache;
 }  // namespace
 
-static pp_status autotune(pp_plan* p) {
+static pp_status autotune(pp_plan* p, bool zmethod_free) {
   int dev = 0;
   cudaGetDevice(&dev);
   {
@@ -683,6 +791,7 @@ static pp_status autotune(pp_plan* p) {
       if (e.dev == dev && e.nx == p->nx && e.ny == p->ny && e.nz == p->nz && e.dtype == p->dtype &&
           memcmp(e.bc, p->bc, sizeof e.bc) == 0) {
         choose_shapes(p, &e.best);
+        if (zmethod_free) p->zmethod = e.zmethod;
         return PP_OK;
       }
   }
@@ -760,6 +869,17 @@ static pp_status autotune(pp_plan* p) {
     if (run_stage(p, stage, f, u, 0, st) != PP_OK) break;  // leave this stage's output for the next one
   }
   const float bx = std::max(bt[0], bt[3]), by = std::max(bt[1], bt[2]);
+  // periodic z: Sherman-Morrison sweeps or the z transform, unless the caller chose one
+  int zbest = p->zmethod;
+  if (p->zfft_ok && zmethod_free) {
+    float tz[2];
+    for (int m = 0; m < 2; m++) {
+      p->zmethod = m;
+      tz[m] = time_stage(2);
+    }
+    zbest = (tz[ZM_FFT] < tz[ZM_SM]) ? ZM_FFT : ZM_SM;
+  }
+  p->zmethod = zbest;
   cudaStreamSynchronize(st);
   cleanup();
   // the timing runs' status (scratch data) is not the caller's
@@ -771,6 +891,7 @@ static pp_status autotune(pp_plan* p) {
   ent.dev = dev; ent.nx = p->nx; ent.ny = p->ny; ent.nz = p->nz; ent.dtype = p->dtype;
   memcpy(ent.bc, p->bc, sizeof ent.bc);
   ent.best = best;
+  ent.zmethod = p->zmethod;
   g_tune_cache.push_back(ent);
   return PP_OK;
 }
@@ -828,9 +949,11 @@ pp_status pp_plan_create(pp_plan** out, int nx, int ny, int nz, const pp_bc bc[6
   for (int a = 0; a < 3; a++)
     if ((bc[2 * a] == PP_BC_PERIODIC) != (bc[2 * a + 1] == PP_BC_PERIODIC))
       return fail(PP_ERR_BC_PAIRING, "axis %d: periodic must be given on both faces", a);
-  if (opt)
-    for (int i = 0; i < 3; i++)
+  if (opt) {
+    for (int i = 0; i < 2; i++)
       if (opt->reserved[i]) return fail(PP_ERR_INVALID_ARG, "options.reserved must be zero");
+    if (opt->z_method < 0 || opt->z_method > 2) return fail(PP_ERR_INVALID_ARG, "options.z_method must be 0, 1 or 2");
+  }
   const int tmax = 512;
   if (opt) {
     for (int v : {opt->threads_x, opt->threads_y, opt->threads_x_inv, opt->threads_y_inv})
@@ -850,6 +973,12 @@ pp_status pp_plan_create(pp_plan** out, int nx, int ny, int nz, const pp_bc bc[6
   // line counts of one launch are 32-bit: x lines ny*nz, y lines (nx + 2)*nz at most
   if ((long long)ny * nz >= (1LL << 31) || (long long)(nx + 2) * nz >= (1LL << 31))
     return fail(PP_ERR_UNSUPPORTED_SIZE, "too many lines per launch (ny*nz and (nx+2)*nz must be < 2^31)");
+
+  // periodic z by transform: nz must be a length the line kernels transform (7-smooth, <= 4096)
+  const bool zfft_ok = zper && nz <= 4096 && smooth2357(nz);
+  const int zreq = opt ? opt->z_method : 0;
+  if (zreq == 2 && !zfft_ok)
+    return fail(PP_ERR_UNSUPPORTED_SIZE, "z_method 2 (transform) needs periodic z and nz = 2^a 3^b 5^c 7^d <= 4096");
 
   pp_plan* p = new (std::nothrow) pp_plan();
   if (!p) return fail(PP_ERR_OUT_OF_MEMORY, "host allocation failed");
@@ -876,6 +1005,9 @@ pp_status pp_plan_create(pp_plan** out, int nx, int ny, int nz, const pp_bc bc[6
   if ((s = axis_tables(p, p->kx, nx, false, p->fx, &p->d_tw_x, &p->d_aux_x)) != PP_OK) { free_plan(p); return s; }
   if ((s = axis_tables(p, p->ky, ny, p->layout == 0, p->fy, &p->d_tw_y, &p->d_aux_y)) != PP_OK) { free_plan(p); return s; }
   if ((s = z_tables(p)) != PP_OK) { free_plan(p); return s; }
+  p->zfft_ok = zfft_ok;
+  if (p->zfft_ok && (s = zfft_tables(p)) != PP_OK) { free_plan(p); return s; }
+  p->zmethod = (zreq == 2) ? ZM_FFT : ZM_SM;
   choose_shapes(p, opt);
 
   p->buf_bytes = (size_t)std::max(p->xplane, p->splane) * nz * p->elem;
@@ -889,7 +1021,7 @@ pp_status pp_plan_create(pp_plan** out, int nx, int ny, int nz, const pp_bc bc[6
   }
   cudaMemset(p->d_status, 0, 4 * sizeof(unsigned));
   if (opt && opt->autotune) {
-    pp_status ts = autotune(p);
+    pp_status ts = autotune(p, zreq == 0);
     if (ts != PP_OK) { free_plan(p); return ts; }
   }
   *out = p;
@@ -1130,6 +1262,12 @@ pp_status pp_plan_launch_shapes(const pp_plan* p, int out[8]) {
   const int v[8] = {p->threads_x[0], p->lpc_x[0], p->threads_y[0], p->lpc_y[0],
                     p->threads_y[1], p->lpc_y[1], p->threads_x[1], p->lpc_x[1]};
   for (int i = 0; i < 8; i++) out[i] = v[i];
+  return PP_OK;
+}
+
+pp_status pp_plan_z_method(const pp_plan* p, int* out) {
+  if (!p || !out) return fail(PP_ERR_INVALID_ARG, "NULL plan or pointer");
+  *out = (p->bc[4] != PP_BC_PERIODIC) ? 0 : (p->zmethod == ZM_FFT ? 2 : 1);
   return PP_OK;
 }
 

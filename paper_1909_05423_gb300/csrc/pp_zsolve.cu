@@ -28,57 +28,10 @@
 //
 // All arithmetic is double-float (pp_arith.cuh), whatever the storage type of the spill.
 //
-// Range report: the spill and the double-float pairs have FP32's exponent range.  Every thread
-// keeps the largest |value| of the scaled right-hand sides it reads and of the solutions it
-// writes; the blocks reduce them into two plan-owned words, and the last block of the launch
-// sets the plan's range bit when the largest scaled input lies below 2^-100 (then the low parts,
-// 2^-24 below, are subnormal and the solve loses accuracy norm-wise), or the largest output is
-// above 2^124 / (nx ny) (the inverse transforms, which sum up to 2 nx and 2 ny values, may
-// overflow), or a value is not finite.  The decision is per launch, on the largest magnitudes,
-// so tiny values beside large ones (the tails of a Gaussian source) never raise it.
-#include "pp_internal.h"
+// Range report: see pp_range.cuh (largest scaled input and output per launch).
+#include "pp_range.cuh"
 
 namespace pp {
-
-// m = max(m, |v|) propagating NaN (max.NaN), one FMNMX per tracked value
-__device__ __forceinline__ void track(float& m, float v) {
-  asm("max.NaN.f32 %0, %0, %1;" : "+f"(m) : "f"(fabsf(v)));
-}
-__device__ __forceinline__ float max_nan(float a, float b) {
-  float r;
-  asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
-  return r;
-}
-
-// Block reduction of the two maxima and the per-launch decision of the last block (256 threads).
-__device__ __forceinline__ void z_range_report(const ZArgs& a, float dmax, float umax) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    dmax = max_nan(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-    umax = max_nan(umax, __shfl_xor_sync(0xffffffffu, umax, o));
-  }
-  __shared__ float s_d[8], s_u[8];
-  const int w = (int)threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) { s_d[w] = dmax; s_u[w] = umax; }
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  float D = s_d[0], U = s_u[0];
-  for (int i = 1; i < ((int)blockDim.x + 31) / 32; i++) { D = max_nan(D, s_d[i]); U = max_nan(U, s_u[i]); }
-  // non-negative floats and NaN order as their bit patterns (sign cleared)
-  const unsigned db = __float_as_uint(D) & 0x7fffffffu, ub = __float_as_uint(U) & 0x7fffffffu;
-  unsigned* r = a.rstat;
-  if (db > *reinterpret_cast<volatile unsigned*>(r + 1)) atomicMax(r + 1, db);
-  if (ub > *reinterpret_cast<volatile unsigned*>(r + 2)) atomicMax(r + 2, ub);
-  __threadfence();
-  if (atomicAdd(r + 3, 1u) == gridDim.x - 1) {
-    // last block: every other block fenced its maxima before counting itself
-    __threadfence();
-    const float Dt = __uint_as_float(atomicExch(r + 1, 0u)), Ut = __uint_as_float(atomicExch(r + 2, 0u));
-    atomicExch(r + 3, 0u);
-    const bool bad = !(Dt <= 3.4e38f) || !(Ut <= a.umax) || (Dt > 0.0f && Dt < a.dmin);  // NaN fails <=
-    if (bad) atomicOr(r, kStatusRange);
-  }
-}
 
 // raw spill value -> double-float, and back
 __device__ __forceinline__ df zcvt(float2 v) { return df{v.x, v.y}; }
@@ -296,7 +249,7 @@ template <class S, int MODE>
 __global__ void __launch_bounds__(256, (ZMinBlocks<S, MODE>::v)) k_zsolve(const ZArgs a) {
   float dmax = 0.0f, umax = 0.0f;
   z_line<S, MODE>(a, dmax, umax);
-  z_range_report(a, dmax, umax);
+  range_report(a.rstat, a.dmin, a.umax, gridDim.x, dmax, umax);
 }
 
 template <class S>

@@ -94,3 +94,25 @@ def batched_grids(seed: int, count: int = 64, sides=(32, 48, 64, 96, 128, 192, 2
                 bc += "".join(rng.choice(["N", "D"], size=2))
         out.append(((n[2], n[1], n[0]), bc))
     return out
+
+
+def manufactured_device(shape, spacing, terms, device="cuda"):
+    """manufactured() evaluated with torch on a device (FP64), for grids too large to build on the
+    host; the same products and the same sign convention."""
+    import torch
+    nz, ny, nx = shape
+    dx, dy, dz = spacing
+    ar = lambda n, h: (torch.arange(n, dtype=torch.float64, device=device) + 0.5) * h
+    x = ar(nx, dx)[None, None, :]
+    y = ar(ny, dy)[None, :, None]
+    z = ar(nz, dz)[:, None, None]
+    fn = {"sin": torch.sin, "cos": torch.cos}
+    u = torch.zeros(shape, dtype=torch.float64, device=device)
+    f = torch.zeros(shape, dtype=torch.float64, device=device)
+    for amp, (fx, kx), (fy, ky), (fz, kz) in terms:
+        t = amp * fn[fx](kx * x) * fn[fy](ky * y) * fn[fz](kz * z)
+        u += t
+        f += -(kx * kx + ky * ky + kz * kz) * t
+        del t
+    return u, f
+

@@ -96,3 +96,18 @@ def test_fault_injection_alloc_fails_cleanly(lib, monkeypatch):
     assert st == 4
     assert h.value is None
     assert b"injected" in lib.pp_last_error_string()
+
+
+def test_z_method_validation(lib):
+    """options.z_method: 2 (z transform) needs periodic z and a 7-smooth nz <= 4096; values outside
+    0..2 are rejected.  Both checks return before any device work."""
+    def create(nz, bc, zm):
+        o = _lib.PlanOptions()
+        o.z_method = zm
+        h = ctypes.c_void_p()
+        return lib.pp_plan_create(ctypes.byref(h), 8, 8, nz, _lib.bc_array(bc), 1.0, 1.0, 1.0, 0, ctypes.byref(o)), h
+    for nz, bc, zm, code in ((37, "PPPPPP", 2, 2), (8, "PPPPDD", 2, 2), (8192, "PPPPPP", 2, 2),
+                             (8, "PPPPPP", 3, 1), (8, "PPPPPP", -1, 1)):
+        st, h = create(nz, bc, zm)
+        assert st == code, (nz, bc, zm, st)
+        assert h.value is None
