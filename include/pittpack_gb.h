@@ -115,13 +115,14 @@ pp_status pp_plan_create(pp_plan** out, int nx, int ny, int nz, const pp_bc bc[6
  * by a power of two into that range and u back by the same factor. */
 pp_status pp_solve(pp_plan* plan, const void* f_dev, void* u_dev, pp_stream_t stream);
 
-/* Mixed precision with one residual-refinement step: u0 = solve(f) (FP32 transforms, so u0 is
- * FP32-exact), r = f - A u0 (7-point stencil of Sec. "Mathematical Formulation"; the second
+/* Mixed precision with one residual-refinement step: u0 = solve(f) (FP32 transforms; u0 is kept in
+ * FP32), r = f - A u0 (7-point stencil of Sec. "Mathematical Formulation"; the second
  * differences of u0 are formed exactly, then scaled by 1/h^2 and subtracted from f in double-float
  * arithmetic, so r is accurate to ~2^-46 |f|), delta = solve(r) with FP32 I/O, u = u0 + delta
  * (rounded once to FP64).  The error of u is about the square of the mixed solve's (~1e-13 against
  * the exact discrete solution).  Only for PP_MIXED_F64IO plans (PP_ERR_INVALID_ARG otherwise).  u
- * must not alias f.  The first call on a plan allocates a grid-sized FP32 scratch. */
+ * must not alias f.  The first call on a plan allocates its scratch: u0 and r in FP32, 8 bytes per
+ * cell. */
 pp_status pp_solve_refined(pp_plan* plan, const void* f_dev, void* u_dev, pp_stream_t stream);
 
 /* pp_solve_refined without any device allocation.  (The paper has no counterpart: it is an
@@ -134,7 +135,7 @@ pp_status pp_solve_refined(pp_plan* plan, const void* f_dev, void* u_dev, pp_str
  * pp_solve_refined, step for step.
  *   plan   : a PP_MIXED_F64IO plan (created beforehand; creating a plan does allocate)
  *   f_dev  : input, nx*ny*nz doubles on the device; u_dev: output, same size, must not alias f
- * Limit: nx*ny*nz <= 2,097,152 cells (the FP32 residual of such a grid), else PP_ERR_UNSUPPORTED_SIZE with a
+ * Limit: nx*ny*nz <= 2,097,152 cells (u0 and the residual of such a grid in FP32), else PP_ERR_UNSUPPORTED_SIZE with a
  * message; other errors as pp_solve_refined.  The first call on each device looks up the
  * array's device address (cudaGetSymbolAddress), so make that first call before any stream
  * capture.  All calls share the one array and each call overwrites what it reads, so calls

@@ -180,18 +180,19 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
 cudaError_t launch_zsolve(const pp_plan* p, void* data, int transpose, cudaStream_t st);
 // periodic z by transform: forward z DFT, diagonal solve, inverse z DFT (in place)
 cudaError_t launch_zfft(const pp_plan* p, void* data, cudaStream_t st);
-cudaError_t launch_residual(const pp_plan* p, const void* f, const void* u, void* r, cudaStream_t st);
-cudaError_t launch_add(const pp_plan* p, void* u, const void* d, const void* shift, cudaStream_t st);
+// refinement: r = f - A u0 (f FP64; u0, r FP32), u = u0 + d - shift (u FP64; u0, d FP32)
+cudaError_t launch_residual(const pp_plan* p, const void* f, const void* u0, void* r, cudaStream_t st);
+cudaError_t launch_add(const pp_plan* p, void* u, const void* u0, const void* d, const void* shift, cudaStream_t st);
 // f -= coef * g on the cells next to face `face` (0..5 = x-,x+,y-,y+,z-,z+), in place
 cudaError_t launch_fold_face(void* f, const void* g, int nx, int ny, int nz, int face, double coef, bool f32,
                              cudaStream_t st);
 // n pseudo-random values in [-1, 1) (FP32 or FP64), timing input of the autotuner
 cudaError_t launch_fill(void* x, long long n, bool f32, cudaStream_t st);
-// mean of an FP64 grid: nparts block sums into `partials` (nparts float2), result (hi,lo) into `mean`
+// mean of an FP32 grid: nparts block sums into `partials` (nparts float2), result (hi,lo) into `mean`
 cudaError_t launch_mean(const pp_plan* p, const void* u, void* partials, int nparts, void* mean, cudaStream_t st);
 constexpr int kMeanParts = 1024;
-// the refined solve on caller-provided scratch (resid: nx*ny*nz floats; partials: kMeanParts float2;
-// mean: one float2)
+// the refined solve on caller-provided scratch (resid: 2 nx*ny*nz floats, u0 then the residual /
+// correction; partials: kMeanParts float2; mean: one float2)
 __attribute__((visibility("hidden"))) pp_status solve_refined_core(pp_plan* p, const void* f, void* u, void* resid,
                                                                   void* partials, void* mean, cudaStream_t st);
 // record the calling thread's error detail (returned by pp_last_error_string) and return s

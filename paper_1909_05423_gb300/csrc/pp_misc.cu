@@ -4,9 +4,8 @@
 // face ghost rules (periodic wrap, Neumann u[-1] = u[0], homogeneous Dirichlet u[-1] = -u[0]);
 // then u = u0 + delta with delta = solve(r).
 //
-// The first solve's u0 comes out of FP32 transforms, so every u0 value is an FP32 number.  The
-// kernels read u0 rounded to FP32 (the identity for such values), which makes the stencil's
-// second differences exact: with u0 in FP32, (m - c) and (p - c) are each an exact sum of two
+// The first solve's u0 comes out of FP32 transforms and is kept as FP32 (its x-inverse writes FP32
+// into the refinement scratch).  That makes the stencil's second differences exact: with u0 in FP32, (m - c) and (p - c) are each an exact sum of two
 // FP32 numbers (TwoSum), and their sum is formed in double-float to ~2^-48 of the difference
 // itself.  Only then are the three differences scaled by 1/h^2 and subtracted from f.  Formed the
 // other way round (each neighbour scaled, the sum taken after), the second difference inherits an
@@ -20,7 +19,7 @@ namespace pp {
 
 struct ResArgs {
   const double* f;
-  const double* u;
+  const float* u;  // u0, FP32
   float* r;
   int nx, ny, nz;
   int bc[6];
@@ -40,7 +39,7 @@ __device__ __forceinline__ df second_difference(float m, float c, float p) {
   return d1 + d2;
 }
 
-__device__ __forceinline__ float u32(const double* u, long long i) { return f32_from_double(__ldg(u + i)); }
+__device__ __forceinline__ float u32(const float* u, long long i) { return __ldg(u + i); }
 
 // One x-row per blockIdx.x (rows = ny nz < 2^31), x positions over threads and blockIdx.y.
 __global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
@@ -51,7 +50,7 @@ __global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
   const int j = (int)(row - (unsigned)k * (unsigned)a.ny);
   const long long nxy = (long long)a.nx * a.ny;
   const long long p = (long long)row * a.nx + i;
-  const double* u = a.u;
+  const float* u = a.u;
   const float c = u32(u, p);
   float xm, xp, ym, yp, zm, zp;
   if (i > 0) xm = u32(u, p - 1);
@@ -73,24 +72,25 @@ __global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
   a.r[p] = df_to_f32(r);
 }
 
-// u = fl32(u0) + d (- shift, the mean of u0, when the problem is singular and the result must be
-// mean-free); d is FP32, the sum is formed in double-float and rounded once to FP64.
-__global__ void __launch_bounds__(256) k_add(double* u, const float* d, long long n, const float2* shift) {
+// u = u0 + d (- shift, the mean of u0, when the problem is singular and the result must be
+// mean-free); u0 and d are FP32, their sum is exact in double-float, rounded once to FP64.
+__global__ void __launch_bounds__(256) k_add(double* u, const float* u0, const float* d, long long n,
+                                             const float2* shift) {
   long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   df v;
-  two_sum(f32_from_double(u[p]), __ldg(d + p), v.hi, v.lo);
+  two_sum(__ldg(u0 + p), __ldg(d + p), v.hi, v.lo);
   if (shift) v = v - df{shift->x, shift->y};
   u[p] = df_to_double(v);
 }
 
-// Block partial sums of an FP64 grid in double-float arithmetic (first pass of the mean).
+// Block partial sums of an FP32 grid in double-float arithmetic (first pass of the mean).
 constexpr int kSumThreads = 256;
-__global__ void __launch_bounds__(kSumThreads) k_partial_sum(const double* u, long long n, float2* part) {
+__global__ void __launch_bounds__(kSumThreads) k_partial_sum(const float* u, long long n, float2* part) {
   __shared__ df sh[kSumThreads];
   df acc = df{0.f, 0.f};
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x)
-    acc = acc + df_from_double(__ldg(u + p));
+    acc = acc + df{__ldg(u + p), 0.0f};
   sh[threadIdx.x] = acc;
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
@@ -126,7 +126,7 @@ static void split_h(double v, float* o) {
 
 cudaError_t launch_residual(const pp_plan* p, const void* f, const void* u, void* r, cudaStream_t st) {
   ResArgs a;
-  a.f = (const double*)f; a.u = (const double*)u; a.r = (float*)r;
+  a.f = (const double*)f; a.u = (const float*)u; a.r = (float*)r;
   a.nx = p->nx; a.ny = p->ny; a.nz = p->nz;
   for (int i = 0; i < 6; i++) a.bc[i] = p->bc[i];
   split_h(1.0 / (p->dx * p->dx), a.ix2);
@@ -141,7 +141,7 @@ cudaError_t launch_residual(const pp_plan* p, const void* f, const void* u, void
 
 cudaError_t launch_mean(const pp_plan* p, const void* u, void* partials, int nparts, void* mean, cudaStream_t st) {
   long long n = (long long)p->nx * p->ny * p->nz;
-  k_partial_sum<<<nparts, kSumThreads, 0, st>>>((const double*)u, n, (float2*)partials);
+  k_partial_sum<<<nparts, kSumThreads, 0, st>>>((const float*)u, n, (float2*)partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   float inv[2];
@@ -202,9 +202,10 @@ cudaError_t launch_fill(void* x, long long n, bool f32, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_add(const pp_plan* p, void* u, const void* d, const void* shift, cudaStream_t st) {
+cudaError_t launch_add(const pp_plan* p, void* u, const void* u0, const void* d, const void* shift, cudaStream_t st) {
   long long n = (long long)p->nx * p->ny * p->nz;
-  k_add<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((double*)u, (const float*)d, n, (const float2*)shift);
+  k_add<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((double*)u, (const float*)u0, (const float*)d, n,
+                                                      (const float2*)shift);
   return cudaGetLastError();
 }
 

@@ -16,9 +16,9 @@
 
 namespace {
 
-constexpr size_t kResidBytes = 16u << 20;                        // residual / correction (FP32)
-constexpr long long kMaxPoints = 2097152;                        // cells (8 MiB of the 16 MiB in use)
-static_assert((size_t)kMaxPoints * sizeof(float) <= kResidBytes, "the residual of the largest grid fits");
+constexpr size_t kResidBytes = 16u << 20;                        // u0, then residual / correction (FP32)
+constexpr long long kMaxPoints = 2097152;                        // cells
+static_assert(2 * (size_t)kMaxPoints * sizeof(float) <= kResidBytes, "u0 and the residual of the largest grid fit");
 constexpr size_t kMeanBytes = (pp::kMeanParts + 1) * sizeof(float2);        // partial sums + mean
 constexpr size_t kScratchBytes = kResidBytes + kMeanBytes;
 
@@ -73,7 +73,7 @@ extern "C" pp_status pp_solve_refined_noalloc(pp_plan* p, const void* f, void* u
   void* base = nullptr;
   pp_status s = scratch_address(&base, &err);
   if (s != PP_OK) return set_last_error(s, err.c_str());
-  void* resid = base;                                            // residual, then correction
+  void* resid = base;                                            // u0, then residual / correction
   void* partials = static_cast<unsigned char*>(base) + kResidBytes;
   float2* mean = static_cast<float2*>(partials) + pp::kMeanParts;
   // Every value read is first written by this call (the residual by the residual kernel, each

@@ -714,8 +714,9 @@ cudaError_t launch_zfft(const pp_plan* p, void* data, cudaStream_t st) {
 // io: storage of f and u (ST_F64 / ST_F32); -1 = the plan's I/O type.  An FP32-transform plan may
 // also run with FP32 I/O (the refinement step's correction solve).
 static pp_status run_stage(pp_plan* p, int stage, const void* f, void* u, int transpose, cudaStream_t st,
-                           int z0 = 0, int nzc = -1, int io = -1) {
+                           int z0 = 0, int nzc = -1, int io = -1, int io_out = -1) {
   if (io < 0) io = (p->dtype == PP_MIXED_F32IO) ? ST_F32 : ST_F64;
+  if (io_out < 0) io_out = io;
   cudaError_t e = cudaSuccess;
   static const char* names[] = {"x-forward", "y-forward", "z-solve", "y-inverse", "x-inverse"};
   switch (stage) {
@@ -726,16 +727,17 @@ static pp_status run_stage(pp_plan* p, int stage, const void* f, void* u, int tr
       e = (p->zmethod == ZM_FFT) ? launch_zfft(p, p->bufB, st) : launch_zsolve(p, p->bufB, transpose, st);
       break;
     case 3: e = launch_lines(p, 1, 1, ST_SPILL, ST_SPILL, p->bufB, p->bufA, st, z0, nzc); break;
-    case 4: e = launch_lines(p, 0, 1, ST_SPILL, io, p->bufA, u, st, z0, nzc); break;
+    case 4: e = launch_lines(p, 0, 1, ST_SPILL, io_out, p->bufA, u, st, z0, nzc); break;
     default: return fail(PP_ERR_INVALID_ARG, "stage %d out of range", stage);
   }
   if (e != cudaSuccess) return fail(PP_ERR_CUDA, "%s launch: %s", names[stage], cudaGetErrorString(e));
   return PP_OK;
 }
 
-static pp_status run_pipeline(pp_plan* p, const void* f, void* u, int transpose, cudaStream_t st, int io = -1) {
+static pp_status run_pipeline(pp_plan* p, const void* f, void* u, int transpose, cudaStream_t st, int io = -1,
+                              int io_out = -1) {
   for (int s = 0; s < 5; s++) {
-    pp_status r = run_stage(p, s, f, u, transpose, st, 0, -1, io);
+    pp_status r = run_stage(p, s, f, u, transpose, st, 0, -1, io, io_out);
     if (r != PP_OK) return r;
   }
   return PP_OK;
@@ -743,26 +745,29 @@ static pp_status run_pipeline(pp_plan* p, const void* f, void* u, int transpose,
 
 namespace pp {
 // The refined solve on caller-provided scratch (pp_solve_refined and pp_solve_refined_noalloc):
-// u0 = solve(f) into u (FP64; FP32-exact values), r = f - A fl32(u0) into resid (FP32), the
-// correction solve delta = solve(r) in place with FP32 I/O, u = u0 + delta (- mean u0 when
-// singular).  resid: nx*ny*nz floats; partials: kMeanParts float2; mean: one float2.
-pp_status solve_refined_core(pp_plan* p, const void* f, void* u, void* resid, void* partials, void* mean,
+// u0 = solve(f) with FP32 output into the first half of scratch, r = f - A u0 into the second half
+// (FP32), the correction solve delta = solve(r) in place with FP32 I/O, u = u0 + delta (- mean u0
+// when singular).  scratch: 2 nx*ny*nz floats; partials: kMeanParts float2; mean: one float2.
+pp_status solve_refined_core(pp_plan* p, const void* f, void* u, void* scratch, void* partials, void* mean,
                              cudaStream_t st) {
-  pp_status s = run_pipeline(p, f, u, 0, st);
+  const size_t n = (size_t)p->nx * p->ny * p->nz;
+  float* u0 = static_cast<float*>(scratch);
+  float* r = u0 + n;
+  pp_status s = run_pipeline(p, f, u0, 0, st, ST_F64, ST_F32);
   if (s != PP_OK) return s;
-  cudaError_t e = launch_residual(p, f, u, resid, st);
+  cudaError_t e = launch_residual(p, f, u0, r, st);
   if (e != cudaSuccess) return fail(PP_ERR_CUDA, "residual launch: %s", cudaGetErrorString(e));
-  s = run_pipeline(p, resid, resid, 0, st, ST_F32);
+  s = run_pipeline(p, r, r, 0, st, ST_F32);
   if (s != PP_OK) return s;
   // A singular problem is solved for the mean-free u; the FP32 first solve leaves a constant offset
   // that the refinement step cannot see (it lies in the null space), so it is removed explicitly.
   const void* shift = nullptr;
   if (p->singular) {
-    e = launch_mean(p, u, partials, kMeanParts, mean, st);
+    e = launch_mean(p, u0, partials, kMeanParts, mean, st);
     if (e != cudaSuccess) return fail(PP_ERR_CUDA, "mean launch: %s", cudaGetErrorString(e));
     shift = mean;
   }
-  e = launch_add(p, u, resid, shift, st);
+  e = launch_add(p, u, u0, r, shift, st);
   if (e != cudaSuccess) return fail(PP_ERR_CUDA, "update launch: %s", cudaGetErrorString(e));
   return PP_OK;
 }
@@ -1079,7 +1084,7 @@ pp_status pp_solve_refined(pp_plan* p, const void* f, void* u, pp_stream_t strea
   if (p->dtype != PP_MIXED_F64IO) return fail(PP_ERR_INVALID_ARG, "refinement needs a PP_MIXED_F64IO plan");
   if (f == u) return fail(PP_ERR_INVALID_ARG, "u must not alias f for the refined solve");
   if (!p->d_resid) {
-    size_t bytes = (size_t)p->nx * p->ny * p->nz * sizeof(float);
+    size_t bytes = 2 * (size_t)p->nx * p->ny * p->nz * sizeof(float);
     cudaError_t e = cudaMalloc(&p->d_resid, bytes);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_mean, (kMeanParts + 1) * sizeof(float2));
     if (e != cudaSuccess) return fail(PP_ERR_OUT_OF_MEMORY, "residual buffer (%zu bytes): %s", bytes, cudaGetErrorString(e));
