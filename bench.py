@@ -344,7 +344,9 @@ def _config2_256(pp, args):
 
 def _config4(pp, workloads, args):
     """64 independent grids, sides drawn from {32,...,256} per axis and boundary conditions per axis/face,
-    U[-1,1] sources; one graph launch per batch (FP64 and FP32 I/O); every plan autotuned."""
+    U[-1,1] sources; one graph launch per batch (FP64 and FP32 I/O), with autotuned plans and with the
+    heuristic launch shapes (the autotuner times each stage alone or as concurrent copies of itself;
+    inside the batch graph the FP64 members ran faster with the heuristic shapes, measured)."""
     import torch
     grids = workloads.batched_grids(seed=4, count=64)
     pts = sum(s[0] * s[1] * s[2] for s, _ in grids)
@@ -352,14 +354,19 @@ def _config4(pp, workloads, args):
     g = torch.Generator(device="cuda")
     g.manual_seed(4)
     for dtype, tdt in (("f64", torch.float64), ("mixed_f32io", torch.float32)):
-        tune = {} if args.no_autotune else {"autotune": 1}
-        plans = [pp.Plan(s, bc, (1.0 / s[2], 1.0 / s[1], 1.0 / s[0]), dtype, options=tune) for s, bc in grids]
         fs = [torch.empty(s, dtype=tdt, device="cuda").uniform_(-1.0, 1.0, generator=g) for s, _ in grids]
         us = [torch.empty_like(x) for x in fs]
-        ms = _events_ms(lambda: pp.solve_batched(plans, fs, us), args.steps)
-        out[dtype] = {"ms_per_batch": ms, "gpoints_s": pts / ms / 1e6, "graph_launches_per_batch": 1}
-        for p in plans:
-            p.close()
+        res = {}
+        for name, tune in (("autotuned", {"autotune": 1}), ("heuristic", {})):
+            if args.no_autotune and tune:
+                continue
+            plans = [pp.Plan(s, bc, (1.0 / s[2], 1.0 / s[1], 1.0 / s[0]), dtype, options=tune) for s, bc in grids]
+            ms = _events_ms(lambda: pp.solve_batched(plans, fs, us), args.steps)
+            res[name] = {"ms_per_batch": ms, "gpoints_s": pts / ms / 1e6, "graph_launches_per_batch": 1}
+            for p in plans:
+                p.close()
+        best = min(res, key=lambda k: res[k]["ms_per_batch"])
+        out[dtype] = dict(res[best], shapes=best, **{k: v for k, v in res.items()})
         del fs, us
         torch.cuda.empty_cache()
     return out

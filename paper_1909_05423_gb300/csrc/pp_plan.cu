@@ -820,17 +820,52 @@ static pp_status autotune(pp_plan* p, bool zmethod_free) {
     if (e1) cudaEventDestroy(e1);
   };
   if (ce != cudaSuccess) { cleanup(); return fail(PP_ERR_OUT_OF_MEMORY, "autotune scratch: %s", cudaGetErrorString(ce)); }
-  // time one stage (3 runs after one warm-up), in ms; +inf on a failed launch
+  // Time one stage (3 runs after one warm-up), in ms per launch; +inf on a failed launch.  A stage
+  // whose grid is too small to fill the GPU is timed as K concurrent copies on K streams (time / K):
+  // its throughput when other work shares the GPU, as in a batched graph, rather than the latency
+  // of a lone launch, which favours small tiles that a shared GPU does not reward.  The copies race
+  // on the scratch buffers (in bounds; the values are discarded).
+  constexpr int kTuneStreams = 16;
+  cudaStream_t side[kTuneStreams] = {};
+  cudaEvent_t sev[kTuneStreams] = {};
+  bool side_ok = true;
+  for (int i = 0; i < kTuneStreams && side_ok; i++)
+    side_ok = cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&sev[i], cudaEventDisableTiming) == cudaSuccess;
+  auto stage_ctas = [&](int s0) -> long long {
+    if (s0 == 0 || s0 == 4) return ((long long)p->ny * p->nz + p->lpc_x[s0 == 4] - 1) / p->lpc_x[s0 == 4];
+    const int parts = (p->layout == 0 && p->ky != AX_P) ? 2 : 1;
+    const long long ncols = (p->layout == 0) ? p->nx / 2 + 1 : p->nx;
+    const long long tx = std::max(1, p->lpc_y[s0 == 3] / parts);
+    return (ncols + tx - 1) / tx * p->nz;
+  };
+  int sm_count = 152;
+  cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
   auto time_stage = [&](int s0) -> float {
+    const long long fill = 16LL * sm_count;  // CTAs for several full waves
+    int K = 1;
+    if (side_ok && s0 != 2) {
+      const long long c = std::max(1LL, stage_ctas(s0));
+      K = (int)std::min<long long>(kTuneStreams, (fill + c - 1) / c);
+    }
     float best = 1e30f;
     for (int r = 0; r < 4; r++) {
       cudaEventRecord(e0, st);
-      if (run_stage(p, s0, f, u, 0, st) != PP_OK) return 1e30f;
+      if (K == 1) {
+        if (run_stage(p, s0, f, u, 0, st) != PP_OK) return 1e30f;
+      } else {
+        for (int i = 0; i < K; i++) {
+          cudaStreamWaitEvent(side[i], e0, 0);
+          if (run_stage(p, s0, f, u, 0, side[i]) != PP_OK) return 1e30f;
+          cudaEventRecord(sev[i], side[i]);
+          cudaStreamWaitEvent(st, sev[i], 0);
+        }
+      }
       cudaEventRecord(e1, st);
       if (cudaEventSynchronize(e1) != cudaSuccess) return 1e30f;
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
-      if (r > 0) best = std::min(best, ms);
+      if (r > 0) best = std::min(best, ms / K);
     }
     return best;
   };
@@ -886,6 +921,10 @@ static pp_status autotune(pp_plan* p, bool zmethod_free) {
   }
   p->zmethod = zbest;
   cudaStreamSynchronize(st);
+  for (int i = 0; i < kTuneStreams; i++) {
+    if (side[i]) cudaStreamSynchronize(side[i]), cudaStreamDestroy(side[i]);
+    if (sev[i]) cudaEventDestroy(sev[i]);
+  }
   cleanup();
   // the timing runs' status (scratch data) is not the caller's
   cudaMemset(p->d_status, 0, sizeof(unsigned));
