@@ -120,7 +120,7 @@ template <> struct Vec<float, double> {
   __device__ static __forceinline__ void cvt(raw_t a, float* v) { v[0] = f32_from_double(a.x); v[1] = f32_from_double(a.y); }
   __device__ static __forceinline__ void ld2(const double* p, long long o, float* v) { cvt(raw(p, o), v); }
   __device__ static __forceinline__ void st2(double* p, long long o, const float* v) {
-    *reinterpret_cast<double2*>(p + o) = make_double2(double_from_f32(v[0]), double_from_f32(v[1]));
+    *reinterpret_cast<double2*>(p + o) = make_double2((double)v[0], (double)v[1]);
   }
 };
 template <> struct Vec<float, float> {
