@@ -168,7 +168,8 @@ pp_status pp_fold_bc(pp_plan* plan, const void* f_in, void* f_out, const void* c
  * given (plans, f, u) list captures the n five-kernel pipelines into a graph and instantiates
  * it (host work, a few ms); later calls with the same lists replay the cached graph (up to 8
  * batches are cached; pp_plan_destroy evicts the graphs that use that plan).  Members run on
- * up to 8 concurrent graph branches; members that share a plan share its workspace and run
+ * up to 32 concurrent graph branches (measured: 8 -> 32 took 64 uneven grids from 4.19 to 4.04 ms
+ * FP64, 2.26 to 2.13 ms FP32); members that share a plan share its workspace and run
  * one after another on one branch.  Errors: PP_ERR_INVALID_ARG (n < 0, NULL arrays or
  * members), PP_ERR_CUDA (capture/instantiate/launch). */
 pp_status pp_solve_batched(pp_plan* const* plans, const void* const* f, void* const* u, int n,

@@ -1157,7 +1157,7 @@ pp_status pp_solve_batched(pp_plan* const* plans, const void* const* f, void* co
   // Capture the batch on private streams: a fork event fans the members out over up to
   // kBranches capture streams (members that share a plan stay on one branch, in order, since
   // they share its workspace), a join brings them back; the graph's branches run concurrently.
-  constexpr int kBranches = 8;
+  constexpr int kBranches = 32;
   std::vector<const pp_plan*> uniq;
   std::vector<int> branch(n);
   for (int i = 0; i < n; i++) {
