@@ -103,6 +103,8 @@ struct ZArgs {
   // range status (plan-owned words: [0] status bits, [1] largest |scaled input|, [2] largest |output|
   // (FP32 bits), [3] count of finished blocks); the last block of a launch compares the maxima
   // with dmin / umax and sets kStatusRange in [0]
+  void* ck;               // checkpoints of the double-float sweeps ([nz/8 rounded up][nreal] pairs),
+                          // or NULL for the two-sweep kernel
   unsigned* rstat;
   float dmin;             // 2^-100: below it the double-float low parts are subnormal
   float umax;             // 2^124 / (nx ny): above it the inverse transforms may overflow FP32

@@ -245,6 +245,196 @@ __device__ __forceinline__ void z_line(const ZArgs& a, float& dmax, float& umax)
   }
 }
 
+// Checkpointed sweeps of the double-float spill (FP64-class plans).  The forward sweep leaves the
+// right-hand sides in place and stores the eliminated value only at the end of each batch of ZU
+// planes, in the plan's other spectral buffer (unused while the z stage runs); the back
+// substitution re-reads a batch's right-hand sides, recomputes its eliminated values from the
+// previous batch's checkpoint (in registers, over the raw values it just loaded) and substitutes.
+// HBM traffic per value: 3 + 2/ZU spill values instead of the two-sweep kernel's 4; the recomputed
+// forward step is cheap beside the bandwidth it saves (the double-float sweeps are bound by HBM).
+// Same arithmetic, in the same order, as the two-sweep kernel.
+template <int MODE>
+__device__ __forceinline__ void z_line_ck(const ZArgs& a, float& dmax, float& umax) {
+  using S = float2;
+  long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.nreal) return;
+  const unsigned row = a.fd_row.div((unsigned)s);
+  const int col = (int)(s - (long long)row * a.row_reals);
+  if (col >= a.row_valid) return;
+  const long long mi = (long long)row * a.row_modes + (a.cplx ? (col >> 1) : col);
+  const ZMode& m = a.modes[mi];
+  S* base = reinterpret_cast<S*>(a.data) + s;
+  S* ck = reinterpret_cast<S*>(a.ck) + s;
+  const long long P = a.plane, CP = a.nreal;
+  const int n = a.nz;
+  const df scale = df{a.scale[0], a.scale[1]};
+  const float2* wt = a.wtab + m.woff;
+  if (m.flags & ZF_SINGULAR) {
+    z_singular<S>(base, P, n, scale, wt, dmax, umax);
+    return;
+  }
+  const df winf = f2df(m.winf), wlast = f2df(m.wlast);
+  const int wlen = m.wlen;
+  auto W = [&](int k) -> df {
+    if (k == n - 1) return wlast;
+    if (k < wlen) return f2df(__ldg(wt + k));
+    return winf;
+  };
+  constexpr int ZU = ZBatch<S>::v;
+  const int nb = (n + ZU - 1) / ZU;
+  S cur[ZU], nxt[ZU];
+
+  if constexpr (MODE != 2) {
+    constexpr bool periodic = (MODE == 1);
+    const float2* qt = a.qtab + m.qoff;
+    const int qlen = periodic ? m.qlen : 0;
+    // forward elimination g_k = (s d_k - g_{k-1}) w_k; periodic: y0 = sum q_k s d_k
+    df g = df{0.f, 0.f};
+    df y0 = df{0.f, 0.f};
+    zload<ZU>(cur, base, P, 0, 1, n);
+    for (int j = 0; j < nb; j++) {
+      const int k0 = j * ZU;
+      if (j + 1 < nb) zload<ZU>(nxt, base, P, k0 + ZU, 1, n);
+      if (k0 >= wlen && k0 >= qlen && k0 + ZU < n) {
+#pragma unroll
+        for (int u = 0; u < ZU; u++) {
+          const df d = zcvt(cur[u]) * scale;
+          track(dmax, d.hi);
+          g = (d - g) * winf;
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < ZU; u++) {
+          const int k = k0 + u;
+          if (k < n) {
+            const df d = zcvt(cur[u]) * scale;
+            track(dmax, d.hi);
+            g = (d - g) * W(k);
+            if (periodic && k < qlen) y0 = y0 + f2df(__ldg(qt + k)) * d;
+          }
+        }
+      }
+      ck[j * CP] = make_float2(g.hi, g.lo);  // g at the last row of batch j
+#pragma unroll
+      for (int u = 0; u < ZU; u++) cur[u] = nxt[u];
+    }
+    df c = df{0.f, 0.f}, cg = df{0.f, 0.f};
+    if (periodic) {
+      c = (y0 + g * f2df(m.igam)) * f2df(m.dsm);  // g == y_{n-1}
+      cg = c * f2df(m.gam);
+    }
+    // back substitution u_k = g_k - w_k u_{k+1} (periodic: v_k), batch by batch from the top
+    df u = df{0.f, 0.f};
+    zload<ZU>(cur, base, P, (nb - 1) * ZU, 1, n);
+    for (int j = nb - 1; j >= 0; j--) {
+      const int k0 = j * ZU;
+      if (j > 0) zload<ZU>(nxt, base, P, k0 - ZU, 1, n);
+      df gk = (j == 0) ? df{0.f, 0.f} : f2df(ck[(j - 1) * CP]);
+      const bool fast = k0 >= wlen && k0 >= qlen && k0 + ZU < n;
+      if (fast) {
+#pragma unroll
+        for (int t = 0; t < ZU; t++) {
+          gk = (zcvt(cur[t]) * scale - gk) * winf;
+          cur[t] = make_float2(gk.hi, gk.lo);
+        }
+#pragma unroll
+        for (int t = ZU - 1; t >= 0; t--) {
+          u = zcvt(cur[t]) - winf * u;
+          track(umax, u.hi);
+          zput(base + (k0 + t) * P, u);
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < ZU; t++) {
+          const int k = k0 + t;
+          if (k < n) {
+            gk = (zcvt(cur[t]) * scale - gk) * W(k);
+            cur[t] = make_float2(gk.hi, gk.lo);
+          }
+        }
+#pragma unroll
+        for (int t = ZU - 1; t >= 0; t--) {
+          const int k = k0 + t;
+          if (k < n) {
+            const df gv = zcvt(cur[t]);
+            if (k == n - 1) u = periodic ? gv - c * wlast : gv;
+            else u = gv - W(k) * u;
+            df outv = u;
+            if (periodic && k < qlen) outv = u - cg * f2df(__ldg(qt + k));
+            track(umax, outv.hi);
+            zput(base + k * P, outv);
+          }
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < ZU; t++) cur[t] = nxt[t];
+    }
+  } else {
+    // transposed factorisation: h_k = s d_k - w_{k-1} h_{k-1},  x_k = (h_k - x_{k+1}) w_k
+    df h = df{0.f, 0.f};
+    df wprev = df{0.f, 0.f};
+    zload<ZU>(cur, base, P, 0, 1, n);
+    for (int j = 0; j < nb; j++) {
+      const int k0 = j * ZU;
+      if (j + 1 < nb) zload<ZU>(nxt, base, P, k0 + ZU, 1, n);
+#pragma unroll
+      for (int u = 0; u < ZU; u++) {
+        const int k = k0 + u;
+        if (k < n) {
+          const df d = zcvt(cur[u]) * scale;
+          track(dmax, d.hi);
+          h = (k == 0) ? d : d - wprev * h;
+          wprev = W(k);
+        }
+      }
+      ck[j * CP] = make_float2(h.hi, h.lo);
+#pragma unroll
+      for (int u = 0; u < ZU; u++) cur[u] = nxt[u];
+    }
+    df x = df{0.f, 0.f};
+    zload<ZU>(cur, base, P, (nb - 1) * ZU, 1, n);
+    for (int j = nb - 1; j >= 0; j--) {
+      const int k0 = j * ZU;
+      if (j > 0) zload<ZU>(nxt, base, P, k0 - ZU, 1, n);
+      df hk = (j == 0) ? df{0.f, 0.f} : f2df(ck[(j - 1) * CP]);
+      df wp = (k0 == 0) ? df{0.f, 0.f} : W(k0 - 1);
+#pragma unroll
+      for (int t = 0; t < ZU; t++) {
+        const int k = k0 + t;
+        if (k < n) {
+          const df d = zcvt(cur[t]) * scale;
+          hk = (k == 0) ? d : d - wp * hk;
+          wp = W(k);
+          cur[t] = make_float2(hk.hi, hk.lo);
+        }
+      }
+#pragma unroll
+      for (int t = ZU - 1; t >= 0; t--) {
+        const int k = k0 + t;
+        if (k < n) {
+          const df hv = zcvt(cur[t]);
+          x = (k == n - 1) ? hv * W(k) : (hv - x) * W(k);
+          track(umax, x.hi);
+          zput(base + k * P, x);
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < ZU; t++) cur[t] = nxt[t];
+    }
+  }
+}
+
+// 4 CTAs of 256 threads per SM (64 registers; the Thomas sweeps spill 56 bytes and run faster than
+// at 3 CTAs without spills, measured), 3 for the cyclic sweeps (they would spill 300 bytes at 64)
+template <int MODE> struct ZCkMinBlocks { static constexpr int v = (MODE == 1) ? 3 : 4; };
+
+template <int MODE>
+__global__ void __launch_bounds__(256, (ZCkMinBlocks<MODE>::v)) k_zsolve_ck(const ZArgs a) {
+  float dmax = 0.0f, umax = 0.0f;
+  z_line_ck<MODE>(a, dmax, umax);
+  range_report(a.rstat, a.dmin, a.umax, gridDim.x, dmax, umax);
+}
+
 template <class S, int MODE>
 __global__ void __launch_bounds__(256, (ZMinBlocks<S, MODE>::v)) k_zsolve(const ZArgs a) {
   float dmax = 0.0f, umax = 0.0f;
@@ -265,6 +455,12 @@ cudaError_t launch_zsolve_impl(const ZArgs& a, bool df_spill, bool zper, cudaStr
   const long long grid = (a.nreal + threads - 1) / threads;
   // periodic z is self-adjoint in this factorisation; the transposed sweep is for Thomas only
   const int mode = zper ? 1 : (a.transpose ? 2 : 0);
+  if (df_spill && a.ck) {
+    if (mode == 1) k_zsolve_ck<1><<<(unsigned)grid, threads, 0, st>>>(a);
+    else if (mode == 2) k_zsolve_ck<2><<<(unsigned)grid, threads, 0, st>>>(a);
+    else k_zsolve_ck<0><<<(unsigned)grid, threads, 0, st>>>(a);
+    return cudaGetLastError();
+  }
   return df_spill ? launch_z<float2>(a, mode, (unsigned)grid, threads, st)
                   : launch_z<float>(a, mode, (unsigned)grid, threads, st);
 }
