@@ -272,6 +272,33 @@ __device__ __forceinline__ void for_groups_y(const LineArgs& a, int nl, const Fa
   for_groups<V, KC>(a, nl, fdk, fn);
 }
 
+// for_groups_y with every item's loads issued before any item is converted and stored: the FP32 y
+// kernels' forward pre-processing was bound by load latency (1024^3 y-forward 2.49 -> 2.18 ms,
+// measured); the inverse kinds and the double-float kernels (bound by issue, capped in registers)
+// gained nothing and keep for_groups_y.
+template <class R, int MC, int V, int KC, class LD, class ST>
+__device__ __forceinline__ void for_groups_yb(const LineArgs& a, int nl, const FastDiv& fdk, LD&& ld, ST&& st) {
+  if constexpr (std::is_same<R, float>::value && MC >= 64 && (MC & (MC - 1)) == 0) {
+    constexpr int VPT = ct_values_per_thread(MC, true, false);
+    constexpr int KS = V * (MC / VPT);
+    constexpr int NI = MC / KS;
+    static_assert(KC == MC, "full item sets");
+    const int G = a.lpc / V;
+    if (nl == a.lpc && (G & (G - 1)) == 0 && (int)blockDim.x == KS * G) {
+      const int lg = __ffs(G) - 1;
+      const int L0 = ((int)threadIdx.x & (G - 1)) * V;
+      const int k0 = (int)threadIdx.x >> lg;
+      decltype(ld(0, 0, 0)) r[NI];
+#pragma unroll
+      for (int i = 0; i < NI; i++) r[i] = ld(L0, k0 + KS * i, V);
+#pragma unroll
+      for (int i = 0; i < NI; i++) st(L0, k0 + KS * i, V, r[i]);
+      return;
+    }
+  }
+  for_groups_y<R, MC, V, KC>(a, nl, fdk, [&](int L0, int k, int nv) { st(L0, k, nv, ld(L0, k, nv)); });
+}
+
 // for_items_xb with the team mapping of for_items_x where the tile qualifies (U | the item count).
 // Used by the forward x kinds; the inverse kinds' loops measured slower with it (larger code in the
 // kernel that also converts to FP64).
@@ -406,18 +433,23 @@ __device__ __noinline__ void pre_tile(const LineArgs& a, const Src src, int nl, 
       const long long pos = src.pos;
       if (kind == LK_DCT2 || kind == LK_DST2) {
         const bool dst = (kind == LK_DST2);
-        for_groups_y<R, MC, V, MC>(a, nl, fk, [&](int L0, int k, int nv) {
+        struct RawV { R v0[V], v1[V]; };
+        auto ldv = [&](int L0, int k, int nv) -> RawV {
           const long long b = src.base(L0);
           const int j0 = 2 * k, j1 = 2 * k + 1;
           const int s0 = j0 < M ? 2 * j0 : 2 * N - 1 - 2 * j0;
           const int s1 = j1 < M ? 2 * j1 : 2 * N - 1 - 2 * j1;
-          R v0[V], v1[V];
-          ldn<R>(src.in, b + s0 * pos, nv, v0);
-          ldn<R>(src.in, b + s1 * pos, nv, v1);
+          RawV r;
+          ldn<R>(src.in, b + s0 * pos, nv, r.v0);
+          ldn<R>(src.in, b + s1 * pos, nv, r.v1);
+          return r;
+        };
+        auto stv = [&](int L0, int k, int nv, const RawV& r) {
+          const int j0 = 2 * k, j1 = 2 * k + 1;
 #pragma unroll
           for (int v = 0; v < V; v++) {
             if (v < nv) {
-              R x0 = v0[v], x1 = v1[v];
+              R x0 = r.v0[v], x1 = r.v1[v];
               if (dst) {
                 if (j0 >= M) x0 = Ar<R>::neg(x0);
                 if (j1 >= M) x1 = Ar<R>::neg(x1);
@@ -425,7 +457,8 @@ __device__ __noinline__ void pre_tile(const LineArgs& a, const Src src, int nl, 
               buf[(L0 + v) * ldm + pad(k)] = cx<R>{x0, x1};
             }
           }
-        });
+        };
+        for_groups_yb<R, MC, V, MC>(a, nl, fk, ldv, stv);
         return;
       }
       if (kind == LK_DCT4 || kind == LK_DST4) {
