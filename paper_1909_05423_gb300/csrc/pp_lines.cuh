@@ -354,7 +354,7 @@ __device__ __noinline__ void pre_tile(const LineArgs& a, const Src src, int nl, 
         const bool dst = (kind == LK_DST2);
         using raw_t = typename Vec<R, SI>::raw_t;
         struct Raw { raw_t a, b; };
-        for_items_xbt<R, MC, MC / 2, pre_batch(MC, std::is_same<R, df>::value ? 4 : 2)>(
+        for_items_xbt<R, MC, MC / 2, pre_batch(MC, 4)>(
             a, nl,
             [&](int L, int k) {
               const long long b = src.base(L) + 4LL * k;
