@@ -36,6 +36,13 @@ namespace pp {
 // raw spill value -> double-float, and back
 __device__ __forceinline__ df zcvt(float2 v) { return df{v.x, v.y}; }
 __device__ __forceinline__ df zcvt(float v) { return df{v, 0.0f}; }
+// s v for a spill value v: unnormalised (TwoProd of the leading parts plus the cross term); the
+// subtraction that consumes it reads unnormalised pairs correctly
+__device__ __forceinline__ df zscaled(float2 v, df s) { return mul_u(df{v.x, v.y}, s); }
+__device__ __forceinline__ df zscaled(float v, df s) {
+  const float p = __fmul_rn(v, s.hi);
+  return df{p, __fmaf_rn(v, s.lo, __fmaf_rn(v, s.hi, -p))};
+}
 __device__ __forceinline__ void zput(float2* p, df v) { *p = make_float2(v.hi, v.lo); }
 __device__ __forceinline__ void zput(float* p, df v) { *p = df_to_f32(v); }
 
@@ -146,7 +153,7 @@ __device__ __forceinline__ void z_line(const ZArgs& a, float& dmax, float& umax)
       if (ZFast<S, MODE>::v && k0 >= wlen && k0 >= qlen && k0 + ZU < n) {
 #pragma unroll
         for (int u = 0; u < ZU; u++) {
-          const df d = zcvt(cur[u]) * scale;
+          const df d = zscaled(cur[u], scale);
           track(dmax, d.hi);
           g = (d - g) * winf;
           zput(base + (k0 + u) * P, g);
@@ -156,7 +163,7 @@ __device__ __forceinline__ void z_line(const ZArgs& a, float& dmax, float& umax)
         for (int u = 0; u < ZU; u++) {
           const int k = k0 + u;
           if (k < n) {
-            df d = zcvt(cur[u]) * scale;
+            df d = zscaled(cur[u], scale);
             track(dmax, d.hi);
             g = (d - g) * W(k);
             if (periodic && k < qlen) y0 = y0 + f2df(__ldg(qt + k)) * d;
