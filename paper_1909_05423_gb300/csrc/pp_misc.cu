@@ -31,12 +31,14 @@ struct ResArgs {
 __device__ __forceinline__ float ghost_or(int bc, float c) { return bc == 1 ? c : -c; }
 
 // (m - c) + (p - c) for FP32 m, c, p: each difference exactly as an unevaluated pair (TwoSum), the
-// two pairs summed in double-float (relative error ~2^-48 of the result)
+// two pairs summed in double-float (relative error ~2^-48 of the result).  The sums and products
+// below use the unnormalised forms of pp_arith.cuh (hi + lo keeps the value; only the final
+// rounding to FP32 needs it normalised).
 __device__ __forceinline__ df second_difference(float m, float c, float p) {
   df d1, d2;
   two_sum(m, -c, d1.hi, d1.lo);
   two_sum(p, -c, d2.hi, d2.lo);
-  return d1 + d2;
+  return add_u(d1, d2);
 }
 
 __device__ __forceinline__ float u32(const float* u, long long i) { return __ldg(u + i); }
@@ -65,10 +67,10 @@ __global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
   else zm = (a.bc[4] == 0) ? u32(u, p + (long long)(a.nz - 1) * nxy) : ghost_or(a.bc[4], c);
   if (k < a.nz - 1) zp = u32(u, p + nxy);
   else zp = (a.bc[5] == 0) ? u32(u, p - (long long)(a.nz - 1) * nxy) : ghost_or(a.bc[5], c);
-  const df lap = second_difference(xm, c, xp) * df{a.ix2[0], a.ix2[1]} +
-                 second_difference(ym, c, yp) * df{a.iy2[0], a.iy2[1]} +
-                 second_difference(zm, c, zp) * df{a.iz2[0], a.iz2[1]};
-  const df r = df_from_double(__ldg(a.f + p)) - lap;
+  const df lap = add_u(add_u(mul_u(second_difference(xm, c, xp), df{a.ix2[0], a.ix2[1]}),
+                              mul_u(second_difference(ym, c, yp), df{a.iy2[0], a.iy2[1]})),
+                        mul_u(second_difference(zm, c, zp), df{a.iz2[0], a.iz2[1]}));
+  const df r = add_u(df_from_double(__ldg(a.f + p)), -lap);
   a.r[p] = df_to_f32(r);
 }
 

@@ -1,0 +1,75 @@
+"""1024^3 parity against the CPU oracle on the bench's own workload: the FP64 path in the bench's
+launch configuration (autotuned plan) against the oracle's solution stored at 100 000 seeded cells
+(every edge cell, whole z-columns, x-lines and y-lines, 4000 cells of each face, random interior
+cells) and its norm (tests/golden/fullsize_1024_nnddnn.txt, written by make_fullsize_1024.py, which
+calls only the oracle).  Source: workloads.uniform_source((1024,)*3, seed=2) -- numpy U[-1,1], mean
+removed -- Neumann-x / Dirichlet-y / Neumann-z, spacing 1/1024."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1909_05423_gb300 import workloads
+from tests.gpu_common import need_gpu, torch
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLDEN = os.path.join(HERE, "golden", "fullsize_1024_nnddnn.txt")
+N = 1024
+
+
+def _golden():
+    stats, idx, vals = {}, [], []
+    with open(GOLDEN) as fh:
+        for line in fh:
+            if line.startswith("#"):
+                continue
+            a, b = line.split()
+            if a in ("norm2", "sum", "maxabs"):
+                stats[a] = float(b)
+            else:
+                idx.append(int(a))
+                vals.append(float(b))
+    return stats, np.asarray(idx, dtype=np.int64), np.asarray(vals)
+
+
+@pytest.fixture(scope="module")
+def solved():
+    need_gpu()
+    import paper_1909_05423_gb300 as pp
+    stats, idx, vals = _golden()
+    f = workloads.uniform_source((N, N, N), seed=2)
+    ft = torch.from_numpy(f).cuda()
+    del f
+    out = {}
+    for dtype in ("f64", "mixed_f64io"):
+        plan = pp.Plan((N, N, N), "NNDDNN", (1.0 / N,) * 3, dtype, options={"autotune": 1})
+        u = plan.solve(ft)
+        torch.cuda.synchronize()
+        plan.status()
+        flat = u.view(-1)
+        out[dtype] = (flat[torch.from_numpy(idx).cuda()].cpu().numpy(), torch.linalg.vector_norm(flat).item(),
+                      flat.sum().item())
+        plan.close()
+        del u, flat
+        torch.cuda.empty_cache()
+    del ft
+    torch.cuda.empty_cache()
+    return stats, idx, vals, out
+
+
+def test_golden_cells_f64(solved):
+    stats, idx, vals, out = solved
+    got, norm, total = out["f64"]
+    assert idx.size == 100000 and np.unique(idx).size == idx.size
+    err = np.abs(got - vals)
+    assert err.max() <= 1e-12 * stats["maxabs"], (err.max(), stats["maxabs"])
+    assert np.linalg.norm(got - vals) <= 1e-12 * np.linalg.norm(vals)
+    assert abs(norm - stats["norm2"]) <= 1e-12 * stats["norm2"], (norm, stats["norm2"])
+
+
+def test_golden_cells_mixed(solved):
+    stats, idx, vals, out = solved
+    got, norm, _ = out["mixed_f64io"]
+    assert np.linalg.norm(got - vals) <= 1e-6 * np.linalg.norm(vals)
+    assert abs(norm - stats["norm2"]) <= 1e-6 * stats["norm2"]

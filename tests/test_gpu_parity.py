@@ -370,3 +370,23 @@ def test_magnitude_range(oracle, scale):
     f = workloads.uniform_source(shape, seed=47)
     ref = oracle.solve(f, "NNDDNN", sp) * scale
     assert rel_l2(gpu_solve(f * scale, "NNDDNN", sp), ref) <= TOL_F64
+
+
+def test_plans_on_two_devices(oracle):
+    """Plans created and solved on two devices of one process (the >48 KB shared-memory opt-in of the
+    line kernels is kept per device); skipped where fewer than two GPUs are visible."""
+    import paper_1909_05423_gb300 as pp
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs two visible GPUs")
+    shape = (16, 64, 128)
+    sp = (1.0 / 128, 1.0 / 64, 1.0 / 16)
+    f = workloads.uniform_source(shape, seed=71)
+    ref = oracle.solve(f, "NNDDNN", sp)
+    for dev in (0, 1, 0):
+        with torch.cuda.device(dev):
+            plan = pp.Plan(shape, "NNDDNN", sp, "f64")
+            u = plan.solve(torch.from_numpy(f).cuda(dev))
+            torch.cuda.synchronize(dev)
+            plan.status()
+            assert rel_l2(u.cpu().numpy(), ref) <= TOL_F64, dev
+            plan.close()
