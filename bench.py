@@ -637,13 +637,16 @@ def run_ours(args):
         h2d, d2h = _copy_gbs(fh, uh, f)
         plan.solve_host(fh, uh)
         barrier()
-        t0 = time.perf_counter()
-        ke = max(1, min(args.steps, 3))
-        for _ in range(ke):
+        # each call timed on its own (it synchronises); the median is reported, since the host side
+        # of these shared machines is not quiet (one run saw 230 ms where others saw 93-98 ms)
+        calls = []
+        for _ in range(max(3, min(args.steps, 5))):
+            t0 = time.perf_counter()
             plan.solve_host(fh, uh)
-        dt = (time.perf_counter() - t0) / ke
+            calls.append(time.perf_counter() - t0)
+        dt = statistics.median(calls)
         e2e = {"value": npts / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": npts * 8, "d2h_bytes_per_step": npts * 8,
-               "ms_per_step": dt * 1e3, "h2d_gbs": h2d, "d2h_gbs": d2h,
+               "ms_per_step": dt * 1e3, "ms_per_call": [round(c * 1e3, 2) for c in calls], "h2d_gbs": h2d, "d2h_gbs": d2h,
                "copy_floor_ms": npts * 8 / (h2d * 1e9) * 1e3 + npts * 8 / (d2h * 1e9) * 1e3,
                "host": host.report(fh.data_ptr(), uh.data_ptr())}
         host.unbind()
