@@ -176,10 +176,12 @@ pp_status pp_solve_batched(pp_plan* const* plans, const void* const* f, void* co
                            pp_stream_t stream);
 
 /* Adjoint: g_f = S^T g, where S is the solution operator f -> u.  Runs the transposed
- * pipeline (transposed inverse transforms, transposed tridiagonal factorisation,
- * transposed forward transforms).  Because A is symmetric for periodic, Neumann and
- * Dirichlet faces, S^T = S; the explicit transposed pipeline is what is executed.
- * Same argument rules as pp_solve. */
+ * pipeline: the line transforms, whose unnormalised syntheses are the transposes of the analyses
+ * up to the per-mode weights the z scale absorbs, around the transposed tridiagonal
+ * factorisation (for non-periodic z).  For periodic z the Sherman-Morrison sweep is run as it is
+ * (A' and its rank-one update are symmetric, so that solve is its own transpose), and so is the
+ * z transform (its eigenvalues are even in kz).  A is symmetric for periodic, Neumann and
+ * Dirichlet faces, so S^T = S.  Same argument rules as pp_solve. */
 pp_status pp_solve_adjoint(pp_plan* plan, const void* g_dev, void* gf_dev, pp_stream_t stream);
 
 /* pp_solve on HOST buffers: copies f to the device, solves, copies u back, and synchronises

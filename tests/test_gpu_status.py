@@ -86,3 +86,20 @@ def test_range_flag_quiet_cases():
             _, err = _solve_status(plan, src)
             assert err is None, (dtype, err)
         plan.close()
+
+
+def test_range_flag_z_transform():
+    """The diagonal solve of periodic z by transform reports the same way."""
+    import paper_1909_05423_gb300 as pp
+    n = 32
+    shape = (n, n, n)
+    sp = (1.0 / n,) * 3
+    f = workloads.uniform_source(shape, seed=53)
+    plan = pp.Plan(shape, "PPPPPP", sp, "f64", options={"z_method": 2})
+    assert plan.z_method() == "transform"
+    for scale, flagged in ((1.0, False), (1e-20, False), (1e-32, True), (1e37, True), (1.0, False)):
+        _, err = _solve_status(plan, f * scale)
+        assert (err is not None) == flagged, (scale, err)
+        if flagged:
+            assert err.status == _lib.PP_ERR_RANGE
+    plan.close()
