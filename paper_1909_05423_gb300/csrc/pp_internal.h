@@ -121,6 +121,9 @@ struct ZDiagArgs {
   const float2* lam;   // per real slot: lambda_x/dx^2 + lambda_y/dy^2 of its mode (hi, lo)
   const float2* zeig;  // per kz: (2 cos(2 pi kz/nz) - 2)/dz^2 (hi, lo)
   float scale[2];      // w_x w_y / nz (hi, lo)
+  int row_reals;       // reals per spectral row (padded)
+  int row_valid;       // reals of a row that carry modes (even): later pairs are padding, skipped
+  FastDiv fd_row;
   unsigned* rstat;     // range report (as ZArgs)
   float dmin, umax;
 };

@@ -703,6 +703,10 @@ cudaError_t launch_zfft(const pp_plan* p, void* data, cudaStream_t st) {
   d.lam = p->d_zlam;
   d.zeig = p->d_zeig;
   split2(axis_weight(p->kx, p->nx) * axis_weight(p->ky, p->ny) / p->nz, d.scale);
+  if (p->layout == 1) { d.row_reals = 2 * p->nx; d.row_valid = 2 * p->nx; }
+  else if (p->layout == 0) { d.row_reals = (int)p->xrow; d.row_valid = p->nx + 2; }
+  else { d.row_reals = (int)p->xrow; d.row_valid = p->nx; }
+  d.fd_row = FastDiv::make((unsigned)d.row_reals);
   d.rstat = p->d_status;
   d.dmin = 0x1p-100f;
   d.umax = (float)(0x1p124 / ((double)p->nx * (double)p->ny * (double)p->nz));

@@ -40,6 +40,10 @@ template <class S>
 __device__ __forceinline__ void zdiag_pair(const ZDiagArgs& a, float& dmax, float& umax) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= a.nreal / 2) return;
+  // the padding pairs at the end of a spectral row hold no mode (and whatever the buffer held
+  // before): they are neither solved nor seen by the range report
+  const unsigned row = a.fd_row.div((unsigned)(2 * c));
+  if ((int)(2 * c - (long long)row * a.row_reals) >= a.row_valid) return;
   const int k = (int)blockIdx.y;
   const int km = (k == 0) ? 0 : a.nz - k;
   S* base = reinterpret_cast<S*>(a.data) + 2 * c;

@@ -103,3 +103,28 @@ def test_range_flag_z_transform():
         if flagged:
             assert err.status == _lib.PP_ERR_RANGE
     plan.close()
+
+
+def test_range_flag_ignores_stale_padding():
+    """A plan's spectral rows end in padding slots that no transform writes; memory a closed plan
+    left behind (here: NaN from a non-finite source) must reach neither the solution nor the range
+    report of a new plan whose buffers reuse it."""
+    import paper_1909_05423_gb300 as pp
+    n = 32
+    shape = (n, n, n)
+    sp = (1.0 / n,) * 3
+    f = workloads.uniform_source(shape, seed=54)
+    for zm in (2, 1):
+        for _ in range(3):
+            old = pp.Plan(shape, "PPPPPP", sp, "f64", options={"z_method": zm})
+            g = f.copy()
+            g[:] = math.nan
+            _solve_status(old, g)
+            old.close()
+            plan = pp.Plan(shape, "PPPPPP", sp, "f64", options={"z_method": zm})
+            u, err = _solve_status(plan, f)
+            assert err is None, (zm, err)
+            assert np.isfinite(u.cpu().numpy()).all()
+            _, err = _solve_status(plan, f * 1e-32)
+            assert err is not None and err.status == _lib.PP_ERR_RANGE, zm
+            plan.close()
