@@ -651,7 +651,7 @@ cudaError_t launch_zsolve(const pp_plan* p, void* data, int transpose, cudaStrea
   a.umax = (float)(0x1p124 / ((double)p->nx * (double)p->ny));
   // the checkpointed double-float sweeps keep their checkpoints in the other spectral buffer, which
   // no stage reads between the y-forward (its last reader) and the y-inverse (its next writer)
-  a.ck = (p->dtype == PP_F64 && data == p->bufB) ? p->bufA : nullptr;
+  a.ck = (p->dtype == PP_F64 && data == p->bufB) ? p->bufA : nullptr;  // every pipeline solves z in bufB
   return launch_zsolve_impl(a, p->dtype == PP_F64, p->bc[4] == PP_BC_PERIODIC, st);
 }
 

@@ -97,6 +97,9 @@ __device__ __noinline__ void z_singular(S* base, long long P, int n, df scale, c
   }
 }
 
+// Two-sweep kernel: the forward sweep writes the eliminated values over the right-hand sides, the
+// back substitution reads them back.  It runs for the FP32 spill (mixed plans); the double-float
+// spill runs the checkpointed sweeps below, which share its arithmetic.
 // MODE 0: Thomas; 1: periodic z (Sherman-Morrison); 2: transposed factorisation (adjoint).
 // Batches wholly inside the converged part of the multipliers (and past the q prefix, before the
 // last row) skip the per-row tests.  That is worth its extra registers where the sweeps are bound
@@ -462,14 +465,15 @@ cudaError_t launch_zsolve_impl(const ZArgs& a, bool df_spill, bool zper, cudaStr
   const long long grid = (a.nreal + threads - 1) / threads;
   // periodic z is self-adjoint in this factorisation; the transposed sweep is for Thomas only
   const int mode = zper ? 1 : (a.transpose ? 2 : 0);
-  if (df_spill && a.ck) {
+  if (df_spill) {
+    // the double-float spill always runs the checkpointed sweeps (they need the checkpoint buffer)
+    if (!a.ck) return cudaErrorInvalidValue;
     if (mode == 1) k_zsolve_ck<1><<<(unsigned)grid, threads, 0, st>>>(a);
     else if (mode == 2) k_zsolve_ck<2><<<(unsigned)grid, threads, 0, st>>>(a);
     else k_zsolve_ck<0><<<(unsigned)grid, threads, 0, st>>>(a);
     return cudaGetLastError();
   }
-  return df_spill ? launch_z<float2>(a, mode, (unsigned)grid, threads, st)
-                  : launch_z<float>(a, mode, (unsigned)grid, threads, st);
+  return launch_z<float>(a, mode, (unsigned)grid, threads, st);
 }
 
 }  // namespace pp

@@ -34,7 +34,11 @@ def test_committed_traffic_is_for_the_bench_workload():
         d = json.load(fh)
     assert d["bc"] == bench.BC
     assert set(d["per_launch_bytes_at_1024"]) == {"x-forward", "y-forward", "z-solve", "y-inverse", "x-inverse"}
-    # every line kernel moves at least its algorithmic 2 x 8.59 GB at 1024^3, the z kernel twice that
+    # every line kernel moves at least its algorithmic 2 x 8.59 GB at 1024^3 (read and write the
+    # spectral spill); the checkpointed z sweeps move 3 + 2/8 spill values per value of the 2
     alg = 2 * 8 * 1024 ** 3
     for stage, v in d["per_launch_bytes_at_1024"].items():
-        assert v > (1.9 if stage == "z-solve" else 0.9) * alg
+        if stage == "z-solve":
+            assert 1.5 * alg < v < 1.75 * alg
+        else:
+            assert v > 0.9 * alg
