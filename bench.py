@@ -62,8 +62,8 @@ KERNEL_SOURCES = ("pp_arith.cuh", "pp_fft.cuh", "pp_internal.h", "pp_lines.cuh",
                   "pp_lines_f32_tiny.cu", "pp_lines_df_small.cu",
                   "pp_lines_df_large.cu", "pp_lines_df_any.cu", "pp_lines_df_any57.cu", "pp_lines_f32_small.cu",
                   "pp_lines_f32_large.cu", "pp_lines_f32_any.cu", "pp_lines_f32_any57.cu", "pp_lines_df_ct3a.cu",
-                  "pp_lines_df_ct3b.cu", "pp_lines_f32_ct3a.cu", "pp_lines_f32_ct3b.cu", "pp_zsolve.cu", "pp_misc.cu",
-                  "pp_zfft.cu", "pp_range.cuh")
+                  "pp_lines_df_ct3b.cu", "pp_lines_f32_ct3a.cu", "pp_lines_f32_ct3b.cu", "pp_zsolve.cu", "pp_zpart.cu", "pp_misc.cu",
+                  "pp_zfft.cu", "pp_range.cuh", "pp_zmul.cuh")
 
 
 def _code_only(text: str) -> str:

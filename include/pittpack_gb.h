@@ -85,7 +85,15 @@ typedef struct pp_plan_options {
                       faster of the two, timed), 1 = Sherman-Morrison sweeps, 2 = DFT along z and a
                       diagonal solve (needs nz = 2^a 3^b 5^c 7^d <= 4096, else
                       PP_ERR_UNSUPPORTED_SIZE); ignored for non-periodic z */
-  int reserved[2]; /* must be zero */
+  int z_split;     /* non-periodic z only: 0 = automatic (the Thomas sweeps, or with autotune = 1
+                      the fastest of them and the partitioned solves, timed as a lone launch),
+                      1 = Thomas sweeps, 8 / 16 / 32 = partitioned solve: every z line split into
+                      chunks of that many rows, one thread per chunk, the chunk carries combined by
+                      recursive doubling (log2 of the chunk count levels; see pp_plan_z_split).
+                      Needs nz <= 512 x rows (else PP_ERR_UNSUPPORTED_SIZE); other values
+                      PP_ERR_INVALID_ARG; ignored for periodic z and for the adjoint's transposed
+                      solve, which run the sweeps */
+  int reserved[1]; /* must be zero */
 } pp_plan_options;
 
 typedef struct pp_plan pp_plan;
@@ -233,6 +241,17 @@ pp_status pp_plan_launch_shapes(const pp_plan* plan, int out[8]);
  * sweeps) or 2 (periodic z: DFT along z and a diagonal solve), as chosen by options.z_method or the
  * autotuner.  Errors: PP_ERR_INVALID_ARG (NULL). */
 pp_status pp_plan_z_method(const pp_plan* plan, int* out);
+
+/* The plan's non-periodic z solver: *out = 1 for the Thomas sweeps (one thread per mode runs the
+ * forward elimination and the back substitution along the whole line), or M = 8, 16 or 32 for the
+ * partitioned solve (Sec. "Solution of the Resulting Tridiagonal Matrices", with the sequential
+ * sweep replaced as in the parallel alternatives of Sec. "Cyclic Reduction Technique"): each line
+ * is cut into ceil(nz / M) chunks of M rows, every chunk runs both recurrences of the Thomas
+ * factorisation from a zero carry, and the chunks' affine carry maps are combined by recursive
+ * doubling, ceil(log2(nz / M)) levels.  Same multipliers and results as the sweeps up to rounding;
+ * about three times their arithmetic per value, in exchange for nz / M times the threads.  Chosen
+ * by options.z_split or the autotuner; periodic z reports 1.  Errors: PP_ERR_INVALID_ARG (NULL). */
+pp_status pp_plan_z_split(const pp_plan* plan, int* out);
 
 /* Human-readable detail of the last error on the calling thread ("" if none). */
 const char* pp_last_error_string(void);

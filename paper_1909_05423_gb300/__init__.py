@@ -162,6 +162,12 @@ class Plan:
         _lib.check(_lib.load().pp_plan_z_method(self._h, ctypes.byref(v)))
         return {0: "thomas", 1: "sherman-morrison", 2: "transform"}[v.value]
 
+    def z_split(self) -> int:
+        """Rows per chunk of the partitioned z solve (8, 16 or 32), or 1 for the Thomas sweeps."""
+        v = ctypes.c_int()
+        _lib.check(_lib.load().pp_plan_z_split(self._h, ctypes.byref(v)))
+        return v.value
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             _lib.load().pp_plan_destroy(self._h)

@@ -71,7 +71,8 @@ inline bool ct_length(int M) {
   return p2 || p3;
 }
 
-// Per-mode z-solve descriptor (tables computed on the host in FP64).
+// Per-mode z-solve descriptor (tables computed on the host in FP64).  The multipliers (table
+// prefix, winf, wlast) are stored as w_k, or for ZF_NEAR1 modes as 1 + w_k (pp_zmul.cuh).
 struct ZMode {
   int woff, wlen;     // prefix of Thomas multipliers w_k in the w table
   int qoff, qlen;     // periodic z: prefix of q = A'^{-1} e_0
@@ -83,7 +84,10 @@ struct ZMode {
   int flags;          // ZF_* bits
   int pad;
 };
-enum { ZF_PERIODIC = 1, ZF_SINGULAR = 2 };
+enum { ZF_PERIODIC = 1, ZF_SINGULAR = 2, ZF_NEAR1 = 4 };
+// a mode whose converged multiplier has 1 + w below this stores 1 + w_k: the rounding of a stored
+// w acts like a relative error of about 2^-48 / (1 + w) on the mode's solution, 2^-45 at the bound
+constexpr double kNear1 = 0.125;
 
 struct ZArgs {
   void* data;             // spectral array, in place
@@ -108,6 +112,7 @@ struct ZArgs {
   unsigned* rstat;
   float dmin;             // 2^-100: below it the double-float low parts are subnormal
   float umax;             // 2^124 / (nx ny): above it the inverse transforms may overflow FP32
+  int only_singular;      // 1: solve the singular mode's column only (after a partitioned solve)
 };
 // status bits of a plan's device status word
 constexpr unsigned kStatusRange = 1u;
@@ -128,6 +133,9 @@ struct ZDiagArgs {
   float dmin, umax;
 };
 enum { ZM_SM = 0, ZM_FFT = 1 };  // periodic z: Sherman-Morrison sweeps / z transform
+// partitioned z solve (pp_zpart.cu): chunk count and slots per CTA for rows-per-chunk M
+bool zpart_shape(int nz, int M, int* G, int* lgG, int* P);
+constexpr int kZSplitRows[3] = {8, 16, 32};  // compiled rows-per-chunk variants
 
 }  // namespace pp
 
@@ -175,6 +183,8 @@ struct pp_plan {
   float2* d_zlam;       // per real slot of a plane
   float2* d_zeig;       // per kz
   int threads_z, lpc_z, ldm_z;
+  // non-periodic z: 1 = Thomas sweeps, M = partitioned solve with M rows per chunk
+  int zsplit;
 };
 
 namespace pp {
@@ -183,6 +193,8 @@ namespace pp {
 cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_out, const void* in, void* out,
                          cudaStream_t st, int z0 = 0, int nzc = -1);
 cudaError_t launch_zsolve(const pp_plan* p, void* data, int transpose, cudaStream_t st);
+// the Thomas sweeps of the singular mode alone (the plan's one pinned column)
+cudaError_t launch_zsingular(const pp_plan* p, void* data, cudaStream_t st);
 // periodic z by transform: forward z DFT, diagonal solve, inverse z DFT (in place)
 cudaError_t launch_zfft(const pp_plan* p, void* data, cudaStream_t st);
 // refinement: r = f - A u0 (f FP64; u0, r FP32), u = u0 + d - shift (u FP64; u0, d FP32)

@@ -32,6 +32,7 @@ namespace pp {
 cudaError_t launch_lines_impl(const LineArgs& a, bool df_arith, int oy, int sin, int sout, int threads,
                               cudaStream_t st);
 cudaError_t launch_zsolve_impl(const ZArgs& a, bool df_spill, bool zper, cudaStream_t st);
+cudaError_t launch_zpart_impl(const ZArgs& a, bool df_spill, int M, cudaStream_t st);
 cudaError_t launch_zdiag_impl(const ZDiagArgs& a, bool df_spill, cudaStream_t st);
 }  // namespace pp
 
@@ -275,7 +276,8 @@ static pp_status z_tables(pp_plan* p) {
       if (sing) {
         // rows 1..n-1 with u_0 pinned: b = b_int, last row + h2 for a Neumann top face
         double b_last = zper ? b_int : b_int + h2;
-        m.flags = ZF_SINGULAR;
+        // multipliers about -k/(k+1): stored as 1 + w (pp_zmul.cuh), exact in FP64 (Sterbenz)
+        m.flags = ZF_SINGULAR | ZF_NEAR1;
         m.woff = (int)(wtab.size() / 2);
         int ns = nz - 1;
         double w = 0.0;
@@ -284,7 +286,7 @@ static pp_status z_tables(pp_plan* p) {
           double mm = (r == 0) ? b : b - h2 * w;
           w = h2 / mm;
           float o[2];
-          split2(w, o);
+          split2(1.0 + w, o);
           wtab.push_back(o[0]); wtab.push_back(o[1]);
         }
         m.wlen = ns;
@@ -341,13 +343,17 @@ static pp_status z_tables(pp_plan* p) {
       }
       m.woff = (int)(wtab.size() / 2);
       m.wlen = (int)ws.pre.size();
+      // a weakly dominant mode, whose converged multiplier (the one of most rows, whose rounding
+      // would act on every row alike) lies near -1, stores 1 + w (pp_zmul.cuh)
+      const bool near1 = 1.0 + ws.winf < kNear1;
+      if (near1) m.flags |= ZF_NEAR1;
       for (double w : ws.pre) {
         float o[2];
-        split2(w, o);
+        split2(near1 ? 1.0 + w : w, o);
         wtab.push_back(o[0]); wtab.push_back(o[1]);
       }
-      split2(ws.winf, m.winf);
-      split2(ws.wlast, m.wlast);
+      split2(near1 ? 1.0 + ws.winf : ws.winf, m.winf);
+      split2(near1 ? 1.0 + ws.wlast : ws.wlast, m.wlast);
     }
     if (wtab.size() / 2 > 0x7fffffffULL || qtab.size() / 2 > 0x7fffffffULL)
       return fail(PP_ERR_UNSUPPORTED_SIZE, "z coefficient tables exceed 2^31 entries");
@@ -628,8 +634,7 @@ cudaError_t launch_lines(const pp_plan* p, int axis, int dir, int io_in, int io_
   return launch_lines_impl(a, dfm, 1, io_in, io_out, p->threads_y[dir], st);
 }
 
-cudaError_t launch_zsolve(const pp_plan* p, void* data, int transpose, cudaStream_t st) {
-  ZArgs a;
+static void zsolve_args(const pp_plan* p, void* data, int transpose, ZArgs& a) {
   memset(&a, 0, sizeof a);
   a.data = data;
   a.plane = p->splane;
@@ -652,7 +657,27 @@ cudaError_t launch_zsolve(const pp_plan* p, void* data, int transpose, cudaStrea
   // the checkpointed double-float sweeps keep their checkpoints in the other spectral buffer, which
   // no stage reads between the y-forward (its last reader) and the y-inverse (its next writer)
   a.ck = (p->dtype == PP_F64 && data == p->bufB) ? p->bufA : nullptr;  // every pipeline solves z in bufB
-  return launch_zsolve_impl(a, p->dtype == PP_F64, p->bc[4] == PP_BC_PERIODIC, st);
+}
+
+cudaError_t launch_zsolve(const pp_plan* p, void* data, int transpose, cudaStream_t st) {
+  ZArgs a;
+  zsolve_args(p, data, transpose, a);
+  const bool zper = p->bc[4] == PP_BC_PERIODIC;
+  // the partitioned solve runs the forward factorisation of non-periodic z (the transposed one of
+  // the adjoint stays on the Thomas sweeps); it leaves the singular mode to the pinned sweep
+  if (p->zsplit > 1 && !zper && !transpose) {
+    cudaError_t e = launch_zpart_impl(a, p->dtype == PP_F64, p->zsplit, st);
+    if (e != cudaSuccess || !p->singular) return e;
+    return launch_zsingular(p, data, st);
+  }
+  return launch_zsolve_impl(a, p->dtype == PP_F64, zper, st);
+}
+
+cudaError_t launch_zsingular(const pp_plan* p, void* data, cudaStream_t st) {
+  ZArgs a;
+  zsolve_args(p, data, 0, a);
+  a.only_singular = 1;
+  return launch_zsolve_impl(a, p->dtype == PP_F64, false, st);
 }
 
 // z lines as strided columns: the y-orientation kernels with one "plane" of splane/2 complex columns
@@ -787,23 +812,26 @@ pp_status solve_refined_core(pp_plan* p, const void* f, void* u, void* scratch, 
 namespace {
 struct TuneEnt {
   int dev, nx, ny, nz, dtype, bc[6];
+  bool zmethod_free, zsplit_free;  // the z choices below were timed (else the caller's)
   pp_plan_options best;
-  int zmethod;
+  int zmethod, zsplit;
 };
 std::mutex g_tune_mu;
 std::vector<TuneEnt> g_tune_cache;
 }  // namespace
 
-static pp_status autotune(pp_plan* p, bool zmethod_free) {
+static pp_status autotune(pp_plan* p, bool zmethod_free, bool zsplit_free) {
   int dev = 0;
   cudaGetDevice(&dev);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     for (const TuneEnt& e : g_tune_cache)
       if (e.dev == dev && e.nx == p->nx && e.ny == p->ny && e.nz == p->nz && e.dtype == p->dtype &&
-          memcmp(e.bc, p->bc, sizeof e.bc) == 0) {
+          memcmp(e.bc, p->bc, sizeof e.bc) == 0 && e.zmethod_free == zmethod_free &&
+          e.zsplit_free == zsplit_free) {
         choose_shapes(p, &e.best);
         if (zmethod_free) p->zmethod = e.zmethod;
+        if (zsplit_free) p->zsplit = e.zsplit;
         return PP_OK;
       }
   }
@@ -927,6 +955,21 @@ static pp_status autotune(pp_plan* p, bool zmethod_free) {
     zbest = (tz[ZM_FFT] < tz[ZM_SM]) ? ZM_FFT : ZM_SM;
   }
   p->zmethod = zbest;
+  // non-periodic z: the Thomas sweeps or the partitioned solve with 8 / 16 / 32 rows per chunk,
+  // timed as a lone launch (the partitioned solve trades extra arithmetic for parallelism, which
+  // pays when a plan has too few modes to fill the GPU)
+  if (zsplit_free && p->bc[4] != PP_BC_PERIODIC) {
+    int sbest = 1;
+    float tbest = 1e30f;
+    for (int M : {1, kZSplitRows[0], kZSplitRows[1], kZSplitRows[2]}) {
+      int G, lgG, P;
+      if (M > 1 && !zpart_shape(p->nz, M, &G, &lgG, &P)) continue;
+      p->zsplit = M;
+      const float t = time_stage(2);
+      if (t < tbest) { tbest = t; sbest = M; }
+    }
+    p->zsplit = sbest;
+  }
   cudaStreamSynchronize(st);
   for (int i = 0; i < kTuneStreams; i++) {
     if (side[i]) cudaStreamSynchronize(side[i]), cudaStreamDestroy(side[i]);
@@ -941,8 +984,11 @@ static pp_status autotune(pp_plan* p, bool zmethod_free) {
   TuneEnt ent;
   ent.dev = dev; ent.nx = p->nx; ent.ny = p->ny; ent.nz = p->nz; ent.dtype = p->dtype;
   memcpy(ent.bc, p->bc, sizeof ent.bc);
+  ent.zmethod_free = zmethod_free;
+  ent.zsplit_free = zsplit_free;
   ent.best = best;
   ent.zmethod = p->zmethod;
+  ent.zsplit = p->zsplit;
   g_tune_cache.push_back(ent);
   return PP_OK;
 }
@@ -1001,9 +1047,11 @@ pp_status pp_plan_create(pp_plan** out, int nx, int ny, int nz, const pp_bc bc[6
     if ((bc[2 * a] == PP_BC_PERIODIC) != (bc[2 * a + 1] == PP_BC_PERIODIC))
       return fail(PP_ERR_BC_PAIRING, "axis %d: periodic must be given on both faces", a);
   if (opt) {
-    for (int i = 0; i < 2; i++)
-      if (opt->reserved[i]) return fail(PP_ERR_INVALID_ARG, "options.reserved must be zero");
+    if (opt->reserved[0]) return fail(PP_ERR_INVALID_ARG, "options.reserved must be zero");
     if (opt->z_method < 0 || opt->z_method > 2) return fail(PP_ERR_INVALID_ARG, "options.z_method must be 0, 1 or 2");
+    const int zs = opt->z_split;
+    if (zs != 0 && zs != 1 && zs != kZSplitRows[0] && zs != kZSplitRows[1] && zs != kZSplitRows[2])
+      return fail(PP_ERR_INVALID_ARG, "options.z_split must be 0, 1, 8, 16 or 32 (got %d)", zs);
   }
   const int tmax = 512;
   if (opt) {
@@ -1030,6 +1078,13 @@ pp_status pp_plan_create(pp_plan** out, int nx, int ny, int nz, const pp_bc bc[6
   const int zreq = opt ? opt->z_method : 0;
   if (zreq == 2 && !zfft_ok)
     return fail(PP_ERR_UNSUPPORTED_SIZE, "z_method 2 (transform) needs periodic z and nz = 2^a 3^b 5^c 7^d <= 4096");
+  // partitioned z solve (non-periodic z; ignored for periodic z): at most 512 chunks per line
+  const int sreq = (opt && !zper) ? opt->z_split : 0;
+  if (sreq > 1) {
+    int G, lgG, P;
+    if (!zpart_shape(nz, sreq, &G, &lgG, &P))
+      return fail(PP_ERR_UNSUPPORTED_SIZE, "z_split %d: nz = %d needs more than 512 chunks per line", sreq, nz);
+  }
 
   pp_plan* p = new (std::nothrow) pp_plan();
   if (!p) return fail(PP_ERR_OUT_OF_MEMORY, "host allocation failed");
@@ -1059,6 +1114,7 @@ pp_status pp_plan_create(pp_plan** out, int nx, int ny, int nz, const pp_bc bc[6
   p->zfft_ok = zfft_ok;
   if (p->zfft_ok && (s = zfft_tables(p)) != PP_OK) { free_plan(p); return s; }
   p->zmethod = (zreq == 2) ? ZM_FFT : ZM_SM;
+  p->zsplit = (sreq > 1) ? sreq : 1;
   choose_shapes(p, opt);
 
   p->buf_bytes = (size_t)std::max(p->xplane, p->splane) * nz * p->elem;
@@ -1072,7 +1128,7 @@ pp_status pp_plan_create(pp_plan** out, int nx, int ny, int nz, const pp_bc bc[6
   }
   cudaMemset(p->d_status, 0, 4 * sizeof(unsigned));
   if (opt && opt->autotune) {
-    pp_status ts = autotune(p, zreq == 0);
+    pp_status ts = autotune(p, zreq == 0, sreq == 0 && !zper);
     if (ts != PP_OK) { free_plan(p); return ts; }
   }
   *out = p;
@@ -1319,6 +1375,12 @@ pp_status pp_plan_launch_shapes(const pp_plan* p, int out[8]) {
 pp_status pp_plan_z_method(const pp_plan* p, int* out) {
   if (!p || !out) return fail(PP_ERR_INVALID_ARG, "NULL plan or pointer");
   *out = (p->bc[4] != PP_BC_PERIODIC) ? 0 : (p->zmethod == ZM_FFT ? 2 : 1);
+  return PP_OK;
+}
+
+pp_status pp_plan_z_split(const pp_plan* p, int* out) {
+  if (!p || !out) return fail(PP_ERR_INVALID_ARG, "NULL plan or pointer");
+  *out = (p->bc[4] == PP_BC_PERIODIC) ? 1 : p->zsplit;
   return PP_OK;
 }
 

@@ -25,7 +25,7 @@ __device__ __forceinline__ float max_nan(float a, float b) {
   return r;
 }
 
-// Block reduction of the two maxima (blocks of at most 256 threads, every thread calls it) and
+// Block reduction of the two maxima (blocks of at most 1024 threads, every thread calls it) and
 // the per-launch decision of the last block.  rstat: [0] status bits, [1] / [2] running maxima
 // (FP32 bits), [3] count of finished blocks; nblocks: blocks of the launch.
 __device__ __forceinline__ void range_report(unsigned* rstat, float dmin, float umax_lim, unsigned nblocks,
@@ -35,7 +35,7 @@ __device__ __forceinline__ void range_report(unsigned* rstat, float dmin, float 
     dmax = max_nan(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
     umax = max_nan(umax, __shfl_xor_sync(0xffffffffu, umax, o));
   }
-  __shared__ float s_d[8], s_u[8];
+  __shared__ float s_d[32], s_u[32];
   const int w = (int)threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0) { s_d[w] = dmax; s_u[w] = umax; }
   __syncthreads();

@@ -30,6 +30,7 @@
 //
 // Range report: see pp_range.cuh (largest scaled input and output per launch).
 #include "pp_range.cuh"
+#include "pp_zmul.cuh"
 
 namespace pp {
 
@@ -68,26 +69,38 @@ __device__ __forceinline__ void zload(S* v, const S* base, long long P, int k0, 
 template <class S>
 __device__ __noinline__ void z_singular(S* base, long long P, int n, df scale, const float2* wt, float& dmax,
                                         float& umax) {
+  // The pinned system is consistent only for a zero-mean right-hand side; a remainder c of the mean
+  // would add a profile growing like c k^2 / 2.  One double-float pass leaves the rounding of a sum
+  // of n values of the source's own mean magnitude (relative 2^-48 per term), so a second pass takes
+  // the mean of the residuals, which are of the size of the fluctuations.
+  const df rn = df_rcp(df{(float)n, 0.f});
   df sum = df{0.f, 0.f};
   for (int k = 0; k < n; k++) sum = sum + zcvt(base[k * P]);
-  df mean = sum * df_rcp(df{(float)n, 0.f});
+  df mean = sum * rn;
+  df rsum = df{0.f, 0.f};
+  for (int k = 0; k < n; k++) rsum = rsum + (zcvt(base[k * P]) - mean);
+  mean = mean + rsum * rn;
   // rows 1..n-1 of the pinned system; multipliers of the sub-system in the table
   df g = df{0.f, 0.f};
   for (int k = 1; k < n; k++) {
     df d = (zcvt(base[k * P]) - mean) * scale;
     track(dmax, d.hi);
-    g = (d - g) * f2df(__ldg(wt + (k - 1)));
+    g = zw_mul<true>(d - g, f2df(__ldg(wt + (k - 1))));  // the pinned table is stored as 1 + w
     zput(base + k * P, g);
   }
   df u = df{0.f, 0.f};
   df usum = df{0.f, 0.f};
   for (int k = n - 1; k >= 1; k--) {
     df gk = zcvt(base[k * P]);
-    u = (k == n - 1) ? gk : gk - f2df(__ldg(wt + (k - 1))) * u;
+    u = (k == n - 1) ? gk : zw_sub<true>(gk, f2df(__ldg(wt + (k - 1))), u);
     usum = usum + u;
     zput(base + k * P, u);
   }
-  df umean = usum * df_rcp(df{(float)n, 0.f});
+  df umean = usum * rn;
+  // the same second pass for the solution's mean (u_0 = 0 is pinned)
+  df ursum = -umean;
+  for (int k = 1; k < n; k++) ursum = ursum + (zcvt(base[k * P]) - umean);
+  umean = umean + ursum * rn;
   zput(base, -umean);
   track(umax, umean.hi);
   for (int k = 1; k < n; k++) {
@@ -113,26 +126,9 @@ template <class S, int MODE> struct ZMinBlocks {
   static constexpr int v = (MODE == 1 && sizeof(S) == 4) ? 2 : (ZFast<S, MODE>::v ? 3 : 4);
 };
 
-template <class S, int MODE>
-__device__ __forceinline__ void z_line(const ZArgs& a, float& dmax, float& umax) {
-  long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= a.nreal) return;
-  // slot s of the (padded) spectral plane -> row, column; padding columns carry no mode
-  const unsigned row = a.fd_row.div((unsigned)s);
-  const int col = (int)(s - (long long)row * a.row_reals);
-  if (col >= a.row_valid) return;
-  const long long mi = (long long)row * a.row_modes + (a.cplx ? (col >> 1) : col);
-  const ZMode& m = a.modes[mi];
-  S* base = reinterpret_cast<S*>(a.data) + s;
-  const long long P = a.plane;
-  const int n = a.nz;
-  const df scale = df{a.scale[0], a.scale[1]};
-  const float2* wt = a.wtab + m.woff;
-  const int flags = m.flags;
-  if (flags & ZF_SINGULAR) {
-    z_singular<S>(base, P, n, scale, wt, dmax, umax);
-    return;
-  }
+template <class S, int MODE, bool N1>
+__device__ __forceinline__ void z_sweeps(const ZArgs& a, const ZMode& m, S* base, long long P, int n, df scale,
+                                         const float2* wt, float& dmax, float& umax) {
   const df winf = f2df(m.winf), wlast = f2df(m.wlast);
   const int wlen = m.wlen;
   auto W = [&](int k) -> df {
@@ -158,7 +154,7 @@ __device__ __forceinline__ void z_line(const ZArgs& a, float& dmax, float& umax)
         for (int u = 0; u < ZU; u++) {
           const df d = zscaled(cur[u], scale);
           track(dmax, d.hi);
-          g = (d - g) * winf;
+          g = zw_mul<N1>(d - g, winf);
           zput(base + (k0 + u) * P, g);
         }
       } else {
@@ -168,7 +164,7 @@ __device__ __forceinline__ void z_line(const ZArgs& a, float& dmax, float& umax)
           if (k < n) {
             df d = zscaled(cur[u], scale);
             track(dmax, d.hi);
-            g = (d - g) * W(k);
+            g = zw_mul<N1>(d - g, W(k));
             if (periodic && k < qlen) y0 = y0 + f2df(__ldg(qt + k)) * d;
             zput(base + k * P, g);
           }
@@ -190,7 +186,7 @@ __device__ __forceinline__ void z_line(const ZArgs& a, float& dmax, float& umax)
       if (ZFast<S, MODE>::v && k0 - ZU + 1 >= wlen && k0 - ZU + 1 >= qlen && k0 < n - 1) {
 #pragma unroll
         for (int t = 0; t < ZU; t++) {
-          u = zcvt(cur[t]) - winf * u;
+          u = zw_sub<N1>(zcvt(cur[t]), winf, u);
           track(umax, u.hi);
           zput(base + (k0 - t) * P, u);
         }
@@ -203,8 +199,8 @@ __device__ __forceinline__ void z_line(const ZArgs& a, float& dmax, float& umax)
         const int k = k0 - t;
         if (k >= 0) {
           const df gk = zcvt(cur[t]);
-          if (k == n - 1) u = periodic ? gk - c * wlast : gk;
-          else u = gk - W(k) * u;
+          if (k == n - 1) u = periodic ? zw_sub<N1>(gk, wlast, c) : gk;
+          else u = zw_sub<N1>(gk, W(k), u);
           df outv = u;
           if (periodic && k < qlen) outv = u - cg * f2df(__ldg(qt + k));
           track(umax, outv.hi);
@@ -227,7 +223,7 @@ __device__ __forceinline__ void z_line(const ZArgs& a, float& dmax, float& umax)
         if (k < n) {
           df d = zcvt(cur[u]) * scale;
           track(dmax, d.hi);
-          h = (k == 0) ? d : d - wprev * h;
+          h = (k == 0) ? d : zw_sub<N1>(d, wprev, h);
           wprev = W(k);
           zput(base + k * P, h);
         }
@@ -244,7 +240,7 @@ __device__ __forceinline__ void z_line(const ZArgs& a, float& dmax, float& umax)
         const int k = k0 - t;
         if (k >= 0) {
           const df hk = zcvt(cur[t]);
-          x = (k == n - 1) ? hk * W(k) : (hk - x) * W(k);
+          x = (k == n - 1) ? zw_mul<N1>(hk, W(k)) : zw_mul<N1>(hk - x, W(k));
           track(umax, x.hi);
           zput(base + k * P, x);
         }
@@ -255,6 +251,39 @@ __device__ __forceinline__ void z_line(const ZArgs& a, float& dmax, float& umax)
   }
 }
 
+// the near -1 form out of line: the few weakly dominant modes of a large grid take a call, and the
+// sweeps of all other modes keep the register allocation of the plain form
+template <class S, int MODE>
+__device__ __noinline__ void z_sweeps_near1(const ZArgs& a, const ZMode& m, S* base, long long P, int n, df scale,
+                                            const float2* wt, float& dmax, float& umax) {
+  z_sweeps<S, MODE, true>(a, m, base, P, n, scale, wt, dmax, umax);
+}
+
+template <class S, int MODE>
+__device__ __forceinline__ void z_line(const ZArgs& a, float& dmax, float& umax) {
+  long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.nreal) return;
+  // slot s of the (padded) spectral plane -> row, column; padding columns carry no mode
+  const unsigned row = a.fd_row.div((unsigned)s);
+  const int col = (int)(s - (long long)row * a.row_reals);
+  if (col >= a.row_valid) return;
+  const long long mi = (long long)row * a.row_modes + (a.cplx ? (col >> 1) : col);
+  const ZMode& m = a.modes[mi];
+  S* base = reinterpret_cast<S*>(a.data) + s;
+  const long long P = a.plane;
+  const int n = a.nz;
+  const df scale = df{a.scale[0], a.scale[1]};
+  const float2* wt = a.wtab + m.woff;
+  const int flags = m.flags;
+  if (a.only_singular && !(flags & ZF_SINGULAR)) return;
+  if (flags & ZF_SINGULAR) {
+    z_singular<S>(base, P, n, scale, wt, dmax, umax);
+    return;
+  }
+  if (flags & ZF_NEAR1) z_sweeps_near1<S, MODE>(a, m, base, P, n, scale, wt, dmax, umax);
+  else z_sweeps<S, MODE, false>(a, m, base, P, n, scale, wt, dmax, umax);
+}
+
 // Checkpointed sweeps of the double-float spill (FP64-class plans).  The forward sweep leaves the
 // right-hand sides in place and stores the eliminated value only at the end of each batch of ZU
 // planes, in the plan's other spectral buffer (unused while the z stage runs); the back
@@ -263,26 +292,11 @@ __device__ __forceinline__ void z_line(const ZArgs& a, float& dmax, float& umax)
 // HBM traffic per value: 3 + 2/ZU spill values instead of the two-sweep kernel's 4; the recomputed
 // forward step is cheap beside the bandwidth it saves (the double-float sweeps are bound by HBM).
 // Same arithmetic, in the same order, as the two-sweep kernel.
-template <int MODE>
-__device__ __forceinline__ void z_line_ck(const ZArgs& a, float& dmax, float& umax) {
+template <int MODE, bool N1>
+__device__ __forceinline__ void z_sweeps_ck(const ZArgs& a, const ZMode& m, float2* base, float2* ck, long long P,
+                                            long long CP, int n, df scale, const float2* wt, float& dmax,
+                                            float& umax) {
   using S = float2;
-  long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= a.nreal) return;
-  const unsigned row = a.fd_row.div((unsigned)s);
-  const int col = (int)(s - (long long)row * a.row_reals);
-  if (col >= a.row_valid) return;
-  const long long mi = (long long)row * a.row_modes + (a.cplx ? (col >> 1) : col);
-  const ZMode& m = a.modes[mi];
-  S* base = reinterpret_cast<S*>(a.data) + s;
-  S* ck = reinterpret_cast<S*>(a.ck) + s;
-  const long long P = a.plane, CP = a.nreal;
-  const int n = a.nz;
-  const df scale = df{a.scale[0], a.scale[1]};
-  const float2* wt = a.wtab + m.woff;
-  if (m.flags & ZF_SINGULAR) {
-    z_singular<S>(base, P, n, scale, wt, dmax, umax);
-    return;
-  }
   const df winf = f2df(m.winf), wlast = f2df(m.wlast);
   const int wlen = m.wlen;
   auto W = [&](int k) -> df {
@@ -310,7 +324,7 @@ __device__ __forceinline__ void z_line_ck(const ZArgs& a, float& dmax, float& um
         for (int u = 0; u < ZU; u++) {
           const df d = zcvt(cur[u]) * scale;
           track(dmax, d.hi);
-          g = (d - g) * winf;
+          g = zw_mul<N1>(d - g, winf);
         }
       } else {
 #pragma unroll
@@ -319,7 +333,7 @@ __device__ __forceinline__ void z_line_ck(const ZArgs& a, float& dmax, float& um
           if (k < n) {
             const df d = zcvt(cur[u]) * scale;
             track(dmax, d.hi);
-            g = (d - g) * W(k);
+            g = zw_mul<N1>(d - g, W(k));
             if (periodic && k < qlen) y0 = y0 + f2df(__ldg(qt + k)) * d;
           }
         }
@@ -344,12 +358,12 @@ __device__ __forceinline__ void z_line_ck(const ZArgs& a, float& dmax, float& um
       if (fast) {
 #pragma unroll
         for (int t = 0; t < ZU; t++) {
-          gk = (zcvt(cur[t]) * scale - gk) * winf;
+          gk = zw_mul<N1>(zcvt(cur[t]) * scale - gk, winf);
           cur[t] = make_float2(gk.hi, gk.lo);
         }
 #pragma unroll
         for (int t = ZU - 1; t >= 0; t--) {
-          u = zcvt(cur[t]) - winf * u;
+          u = zw_sub<N1>(zcvt(cur[t]), winf, u);
           track(umax, u.hi);
           zput(base + (k0 + t) * P, u);
         }
@@ -358,7 +372,7 @@ __device__ __forceinline__ void z_line_ck(const ZArgs& a, float& dmax, float& um
         for (int t = 0; t < ZU; t++) {
           const int k = k0 + t;
           if (k < n) {
-            gk = (zcvt(cur[t]) * scale - gk) * W(k);
+            gk = zw_mul<N1>(zcvt(cur[t]) * scale - gk, W(k));
             cur[t] = make_float2(gk.hi, gk.lo);
           }
         }
@@ -367,8 +381,8 @@ __device__ __forceinline__ void z_line_ck(const ZArgs& a, float& dmax, float& um
           const int k = k0 + t;
           if (k < n) {
             const df gv = zcvt(cur[t]);
-            if (k == n - 1) u = periodic ? gv - c * wlast : gv;
-            else u = gv - W(k) * u;
+            if (k == n - 1) u = periodic ? zw_sub<N1>(gv, wlast, c) : gv;
+            else u = zw_sub<N1>(gv, W(k), u);
             df outv = u;
             if (periodic && k < qlen) outv = u - cg * f2df(__ldg(qt + k));
             track(umax, outv.hi);
@@ -393,7 +407,7 @@ __device__ __forceinline__ void z_line_ck(const ZArgs& a, float& dmax, float& um
         if (k < n) {
           const df d = zcvt(cur[u]) * scale;
           track(dmax, d.hi);
-          h = (k == 0) ? d : d - wprev * h;
+          h = (k == 0) ? d : zw_sub<N1>(d, wprev, h);
           wprev = W(k);
         }
       }
@@ -413,7 +427,7 @@ __device__ __forceinline__ void z_line_ck(const ZArgs& a, float& dmax, float& um
         const int k = k0 + t;
         if (k < n) {
           const df d = zcvt(cur[t]) * scale;
-          hk = (k == 0) ? d : d - wp * hk;
+          hk = (k == 0) ? d : zw_sub<N1>(d, wp, hk);
           wp = W(k);
           cur[t] = make_float2(hk.hi, hk.lo);
         }
@@ -423,7 +437,7 @@ __device__ __forceinline__ void z_line_ck(const ZArgs& a, float& dmax, float& um
         const int k = k0 + t;
         if (k < n) {
           const df hv = zcvt(cur[t]);
-          x = (k == n - 1) ? hv * W(k) : (hv - x) * W(k);
+          x = (k == n - 1) ? zw_mul<N1>(hv, W(k)) : zw_mul<N1>(hv - x, W(k));
           track(umax, x.hi);
           zput(base + k * P, x);
         }
@@ -432,6 +446,38 @@ __device__ __forceinline__ void z_line_ck(const ZArgs& a, float& dmax, float& um
       for (int t = 0; t < ZU; t++) cur[t] = nxt[t];
     }
   }
+}
+
+template <int MODE>
+__device__ __noinline__ void z_sweeps_ck_near1(const ZArgs& a, const ZMode& m, float2* base, float2* ck, long long P,
+                                               long long CP, int n, df scale, const float2* wt, float& dmax,
+                                               float& umax) {
+  z_sweeps_ck<MODE, true>(a, m, base, ck, P, CP, n, scale, wt, dmax, umax);
+}
+
+template <int MODE>
+__device__ __forceinline__ void z_line_ck(const ZArgs& a, float& dmax, float& umax) {
+  using S = float2;
+  long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.nreal) return;
+  const unsigned row = a.fd_row.div((unsigned)s);
+  const int col = (int)(s - (long long)row * a.row_reals);
+  if (col >= a.row_valid) return;
+  const long long mi = (long long)row * a.row_modes + (a.cplx ? (col >> 1) : col);
+  const ZMode& m = a.modes[mi];
+  S* base = reinterpret_cast<S*>(a.data) + s;
+  S* ck = reinterpret_cast<S*>(a.ck) + s;
+  const long long P = a.plane, CP = a.nreal;
+  const int n = a.nz;
+  const df scale = df{a.scale[0], a.scale[1]};
+  const float2* wt = a.wtab + m.woff;
+  if (a.only_singular && !(m.flags & ZF_SINGULAR)) return;
+  if (m.flags & ZF_SINGULAR) {
+    z_singular<S>(base, P, n, scale, wt, dmax, umax);
+    return;
+  }
+  if (m.flags & ZF_NEAR1) z_sweeps_ck_near1<MODE>(a, m, base, ck, P, CP, n, scale, wt, dmax, umax);
+  else z_sweeps_ck<MODE, false>(a, m, base, ck, P, CP, n, scale, wt, dmax, umax);
 }
 
 // 4 CTAs of 256 threads per SM (64 registers; the Thomas sweeps spill 56 bytes and run faster than
@@ -461,8 +507,9 @@ static cudaError_t launch_z(const ZArgs& a, int mode, unsigned grid, int threads
 }
 
 cudaError_t launch_zsolve_impl(const ZArgs& a, bool df_spill, bool zper, cudaStream_t st) {
-  const int threads = 256;
-  const long long grid = (a.nreal + threads - 1) / threads;
+  // the singular mode alone: it is mode (0, 0), real slot 0 (and 1 for a complex mode)
+  const int threads = a.only_singular ? 32 : 256;
+  const long long grid = a.only_singular ? 1 : (a.nreal + threads - 1) / threads;
   // periodic z is self-adjoint in this factorisation; the transposed sweep is for Thomas only
   const int mode = zper ? 1 : (a.transpose ? 2 : 0);
   if (df_spill) {

@@ -111,3 +111,21 @@ def test_z_method_validation(lib):
         st, h = create(nz, bc, zm)
         assert st == code, (nz, bc, zm, st)
         assert h.value is None
+
+
+def test_z_split_validation(lib):
+    """options.z_split: 0, 1, 8, 16 or 32 (else PP_ERR_INVALID_ARG); a partitioned solve takes at
+    most 512 chunks per line (else PP_ERR_UNSUPPORTED_SIZE); reserved must stay zero.  All three
+    checks return before any device work."""
+    def create(nz, zs, reserved=0):
+        o = _lib.PlanOptions()
+        o.z_split = zs
+        o.reserved[0] = reserved
+        h = ctypes.c_void_p()
+        return lib.pp_plan_create(ctypes.byref(h), 8, 8, nz, _lib.bc_array("NNDDNN"), 1.0, 1.0, 1.0, 0,
+                                  ctypes.byref(o)), h
+    for nz, zs, res, code in ((64, 2, 0, 1), (64, 64, 0, 1), (64, -1, 0, 1), (64, 0, 1, 1),
+                              (8 * 512 + 1, 8, 0, 2), (16 * 512 + 1, 16, 0, 2), (32 * 512 + 1, 32, 0, 2)):
+        st, h = create(nz, zs, res)
+        assert st == code, (nz, zs, res, st)
+        assert h.value is None

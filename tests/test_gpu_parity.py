@@ -131,6 +131,37 @@ def test_thomas_z_long_lines(oracle, shape, bc):
     assert rel_l2(gpu_solve(fz, bc, sp), refz) <= TOL_F64
 
 
+@pytest.mark.parametrize("shape", [(4095, 8, 8), (2047, 4, 6)])
+@pytest.mark.parametrize("bc", ["DDNNDD", "NNDDNN", "DDDDDN"])
+def test_weak_modes_long_lines(oracle, shape, bc):
+    """Long z lines on few, coarse x-y modes: with dz much below dx and dy every mode is weakly
+    dominant, its converged multiplier within a few 1e-3 of -1.  Stored as 1 + w those multipliers
+    keep their FP64 values; a plain double-float w would carry a relative error of 2^-48 / (1 + w)
+    into every row alike (1.6e-12 against the oracle at 8 x 8 x 4095, Dirichlet z)."""
+    nz, ny, nx = shape
+    sp = (1.0 / nx, 1.0 / ny, 1.0 / nz)
+    f = workloads.uniform_source(shape, seed=19, remove_mean=False)
+    ref = oracle.solve(f, bc, sp)
+    assert rel_l2(gpu_solve(f, bc, sp), ref) <= TOL_F64
+    assert rel_l2(gpu_solve(f, bc, sp, "mixed_f64io"), ref) <= 1e-6
+
+
+@pytest.mark.parametrize("shape,bc,sp", [((1024, 8, 8), "NNNNNN", None), ((2048, 8, 8), "PPPPPP", None),
+                                         ((300, 12, 16), "NNNNNN", (0.1, 0.2, 0.3)), ((1024, 6, 4), "PPNNNN", None)])
+def test_singular_long_lines_source_mean(oracle, shape, bc, sp):
+    """Singular problems on long z lines with a source of non-zero mean: the (0,0) mode's right-hand
+    side is the plane sums, a large constant plus fluctuations.  The pinned solve needs its exact
+    zero mean (a remainder c grows like c k^2 / 2), which takes a second pass over the residuals
+    (one double-float pass left 1.1e-11 against the oracle at 8 x 8 x 1024)."""
+    nz, ny, nx = shape
+    sp = sp or (1.0 / nx, 1.0 / ny, 1.0 / nz)
+    f = np.random.default_rng(25).uniform(0, 1, size=shape)
+    ref = oracle.solve(f, bc, sp)
+    u = gpu_solve(f, bc, sp)
+    assert abs(u.mean()) <= 1e-13 * np.abs(u).max()
+    assert rel_l2(u, ref) <= TOL_F64
+
+
 def test_singular_zero_mean(oracle):
     shape = (16, 24, 36)
     rng = np.random.default_rng(5)

@@ -213,3 +213,48 @@ def test_thomas_and_cyclic_vs_dense(oracle):
         np.testing.assert_allclose(oracle.thomas(a, b, c, d), np.linalg.solve(T, d), atol=1e-12)
         C = T.copy(); C[0, n - 1] += 0.6; C[n - 1, 0] += 0.8
         np.testing.assert_allclose(oracle.cyclic(a, b, c, 0.8, 0.6, d), np.linalg.solve(C, d), atol=1e-12)
+
+
+def _pinned_exact(g, dz, periodic):
+    """Zero-mean solution of the 1-D cell-centred singular problem (u_{k-1} - 2 u_k + u_{k+1}) / dz^2
+    = g_k - mean(g), Neumann ends (u_{-1} = u_0, u_n = u_{n-1}) or periodic, in exact rational
+    arithmetic: u_0 pinned to 0, rows 1..n-1 by elimination, then the mean subtracted."""
+    from fractions import Fraction as Fr
+    n = len(g)
+    h2 = 1 / (Fr(dz) * Fr(dz))
+    gf = [Fr(float(x)) for x in g]
+    mean = sum(gf) / n
+    d = [x - mean for x in gf]
+    m = n - 1
+    b = [-2 * h2] * m
+    if not periodic:
+        b[-1] = -h2  # Neumann top: the ghost equals the last cell
+    cp, dp = [Fr(0)] * m, [Fr(0)] * m
+    cp[0], dp[0] = h2 / b[0], d[1] / b[0]
+    for i in range(1, m):
+        mm = b[i] - h2 * cp[i - 1]
+        cp[i] = h2 / mm
+        dp[i] = (d[i + 1] - h2 * dp[i - 1]) / mm
+    x = [Fr(0)] * m
+    x[-1] = dp[-1]
+    for i in range(m - 2, -1, -1):
+        x[i] = dp[i] - cp[i] * x[i + 1]
+    u = [Fr(0)] + x
+    mu = sum(u) / n
+    return np.array([float(v - mu) for v in u])
+
+
+@pytest.mark.parametrize("n,tol", [(64, 1e-13), (256, 1e-12)])
+@pytest.mark.parametrize("bcz", ["NN", "PP"])
+def test_singular_mode_exact_rational(oracle, n, tol, bcz):
+    """The pinned singular mode (Sec. "Well-posedness") against exact rational arithmetic: a source
+    constant in x and y with a non-zero mean has only the (0,0) mode, so the oracle's solution is
+    the 1-D zero-mean solution in every column."""
+    rng = np.random.default_rng(n)
+    g = rng.uniform(0, 1, size=n)
+    f = np.broadcast_to(g[:, None, None], (n, 2, 2)).copy()
+    sp = (0.5, 0.5, 1.0 / n)
+    u = oracle.solve(f, "NNNN" + bcz, sp)
+    ue = _pinned_exact(g, sp[2], bcz == "PP")
+    assert np.abs(u - u[:, :1, :1]).max() <= 1e-13 * np.abs(u).max()
+    assert np.linalg.norm(u[:, 0, 0] - ue) / np.linalg.norm(ue) <= tol
