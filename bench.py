@@ -342,6 +342,41 @@ def _config2_256(pp, args):
     return out
 
 
+def _zsolver_study(pp, args):
+    """The paper's tridiagonal-solver comparison (Sec. "Comparison of Tridiagonal Solvers": 64 x 64
+    modes, n_z = 255 .. 4095, one GPU): FP64 solves with the z lines solved by the Thomas sweeps and
+    by the partitioned solve the autotuner picks (chunk rows 8 / 16 / 32), timed per solve and for
+    the z stage alone (in place, on the plan's spectral buffer)."""
+    import ctypes
+    import torch
+    from paper_1909_05423_gb300 import _lib
+    lib = _lib.load()
+    out = []
+    for nz in (255, 511, 1023, 2047, 4095):
+        shape = (nz, 64, 64)
+        sp = (1.0 / 64, 1.0 / 64, 1.0 / nz)
+        g = torch.Generator(device="cuda")
+        g.manual_seed(SEED)
+        f = torch.empty(shape, dtype=torch.float64, device="cuda").uniform_(-1.0, 1.0, generator=g)
+        u = torch.empty_like(f)
+        row = {"nz": nz}
+        for name, opt in (("thomas", {"z_split": 1}), ("autotuned", {"autotune": 1})):
+            plan = pp.Plan(shape, BC, sp, "f64", options=opt)
+            ms = _events_ms(lambda: plan.solve(f, u), 20)
+            plan.status()
+            fp, up = ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(u.data_ptr())
+            zms = _events_ms(lambda: lib.pp_run_stage(plan._h, 2, fp, up, None), 20)
+            try:
+                plan.status()  # repeated in-place z solves of one buffer: the values are discarded
+            except _lib.PPError:
+                pass
+            row[name] = {"solve_ms": ms, "z_ms": zms, "z_split": plan.z_split()}
+            plan.close()
+        row["solve_speedup"] = row["thomas"]["solve_ms"] / row["autotuned"]["solve_ms"]
+        out.append(row)
+    return out
+
+
 def _config4(pp, workloads, args):
     """64 independent grids, sides drawn from {32,...,256} per axis and boundary conditions per axis/face,
     U[-1,1] sources; one graph launch per batch (FP64 and FP32 I/O), with autotuned plans and with the
@@ -622,6 +657,7 @@ def run_ours(args):
         variants["config3_mixed_mms"] = _config3(pp, workloads, args)
         variants["config4_batched"] = _config4(pp, workloads, args)
         variants["config5_adjoint"] = _config5(pp, workloads, args)
+        variants["zsolver_study_64x64"] = _zsolver_study(pp, args)
         u = torch.empty_like(f)
         plan.solve(f, u)
 

@@ -12,19 +12,21 @@
 
 namespace pp {
 
+// In the N1 forms the intermediate product and sum stay unnormalised (exact leading parts, the
+// error terms collected in the low part); the final sum normalises.
 // x w_k for the stored multiplier v (N1: v = 1 + w_k)
 template <bool N1> __device__ __forceinline__ df zw_mul(df x, df v) {
-  if constexpr (N1) return x * v - x;
+  if constexpr (N1) return mul_u(x, v) - x;
   else return x * v;
 }
 // g - w_k u
 template <bool N1> __device__ __forceinline__ df zw_sub(df g, df v, df u) {
-  if constexpr (N1) return (g + u) - v * u;
+  if constexpr (N1) return add_u(g, u) - mul_u(v, u);
   else return g - v * u;
 }
 // x (-w_k), the coefficient of the first-order recurrences of the factorisation
 template <bool N1> __device__ __forceinline__ df zw_neg_mul(df x, df v) {
-  if constexpr (N1) return x - x * v;
+  if constexpr (N1) return x - mul_u(x, v);
   else return x * (-v);
 }
 

@@ -13,7 +13,8 @@
 //   1. every thread runs the recurrence over its chunk from a zero carry, keeping the local
 //      values and the chunk's affine map x_out = A x_in + B (A the product of its a_k);
 //   2. the maps of the P chunks of a line are composed by recursive doubling (Kogge-Stone: at
-//      level j every chunk composes its map with the one 2^j chunks before it, log2 P levels),
+//      level j every chunk composes its map with the one 2^j chunks before it), with warp
+//      shuffles inside a warp's run of chunks and one shared-memory exchange of the warps' totals,
 //      which gives each chunk its true carry;
 //   3. every thread adds (product of a_i up to row k) x carry to its local values.
 // The multipliers and the order of the per-row operations are those of the Thomas sweeps, so the
@@ -22,8 +23,7 @@
 // whose distance from weak diagonal dominance (about the square of the lowest wavenumber)
 // double-float coefficients would not keep.
 //
-// The M values of a thread stay in registers between the steps; the maps are exchanged through
-// shared memory.  A CTA takes G adjacent real slots (consecutive threads: consecutive slots, so
+// The M values of a thread stay in registers between the steps.  A CTA takes G adjacent real slots (consecutive threads: consecutive slots, so
 // every row access of a warp is a few contiguous segments) x P chunks; G P <= 512.  Padding slots
 // take part in the scans with their maps unused; the singular mode's column is left untouched
 // (the plan solves it with the pinned Thomas sweep afterwards).
@@ -41,40 +41,80 @@ __device__ __forceinline__ void zp_st(float* p, df v) { *p = df_to_f32(v); }
 __device__ __forceinline__ df zp_f2(float2 v) { return df{v.x, v.y}; }
 __device__ __forceinline__ df zp_f2(const float* v) { return df{v[0], v[1]}; }
 
-// Inclusive scan of the chunk maps (A, B) of every line of the CTA by recursive doubling.
-// dir = +1: chunk c composes with chunk c - 2^j (forward recurrence, maps applied in increasing
-// chunk order); dir = -1: with chunk c + 2^j (backward recurrence).  Composition: the map of the
-// nearer chunks applied after the farther ones, (A, B) o (A', B') = (A A', A B' + B).
-// sm: 2 G P float2; every thread of the CTA calls it (threads with c >= P, which only round the
-// CTA up to whole warps, take no part).
-__device__ __forceinline__ void zp_scan(df& A, df& B, float2* sm, int c, int col, int G, int P, int dir) {
-  float2* sA = sm;
-  float2* sB = sm + G * P;
-  const int idx = c * G + col;
-  for (int o = 1; o < P; o <<= 1) {
-    if (c < P) {
-      sA[idx] = make_float2(A.hi, A.lo);
-      sB[idx] = make_float2(B.hi, B.lo);
-    }
-    __syncthreads();
-    const int nc = c - dir * o;
-    if (c < P && nc >= 0 && nc < P) {
-      const df An = zp_f2(sA[nc * G + col]), Bn = zp_f2(sB[nc * G + col]);
-      B = A * Bn + B;
-      A = A * An;
-    }
-    __syncthreads();
+// (A, B) pairs of one carry's segment totals: up to 16 warps x 8 lines, two words each
+constexpr int kZpAgg = 2 * 16 * 8;
+
+// Composition of chunk maps x -> A x + B: (X o Y)(x) = X(Y(x)) = (A_X A_Y) x + (A_X B_Y + B_X).
+__device__ __forceinline__ void zp_compose(df& A, df& B, df Ay, df By) {
+  B = A * By + B;
+  A = A * Ay;
+}
+__device__ __forceinline__ df zp_shfl(df v, int delta, bool up) {
+  return up ? df{__shfl_up_sync(0xffffffffu, v.hi, delta), __shfl_up_sync(0xffffffffu, v.lo, delta)}
+            : df{__shfl_down_sync(0xffffffffu, v.hi, delta), __shfl_down_sync(0xffffffffu, v.lo, delta)};
+}
+
+// Carry of every chunk from the chunk maps of its line, by recursive doubling in two levels.  A warp
+// holds CW = 32 / G consecutive chunks of each of the CTA's G lines (lane = chunk-in-warp x G +
+// line), one segment per line; the warp's segments are scanned with shuffles (log2 CW levels: at
+// level o a chunk composes its map with the one o chunks nearer the start of the recurrence), the
+// segment totals are exchanged through shared memory (one barrier), and each chunk composes the
+// totals of the segments before its own.
+// dir = +1 (forward recurrence, starting at chunk 0): returns the value entering the chunk, the
+// output of chunk c - 1 (0 for chunk 0).  dir = -1 (backward recurrence, starting at the last
+// chunk): the output of chunk c + 1 (0 for the last).
+// agg: NS x G pairs of (A, B), NS = warps of the CTA.  Every thread calls it; chunks past the line
+// (c >= P) hold the identity map, which composes away.
+__device__ __forceinline__ df zp_carry(df A, df B, float2* agg, int c, int col, int G, int lgG, int dir) {
+  const int lane = (int)threadIdx.x & 31;
+  const int cw = 32 >> lgG;          // chunks per warp and line
+  const int ci = lane >> lgG;        // chunk within the warp's segment
+  const int seg = (int)threadIdx.x >> 5;
+  const int nseg = ((int)blockDim.x + 31) >> 5;
+  const bool fwd = dir > 0;
+  // 1. inclusive scan within the segment
+  for (int o = 1; o < cw; o <<= 1) {
+    const df An = zp_shfl(A, o * G, fwd), Bn = zp_shfl(B, o * G, fwd);
+    if (fwd ? (ci >= o) : (ci + o < cw)) zp_compose(A, B, An, Bn);
   }
+  // the inclusive map of the neighbouring chunk nearer the start (same segment unless at its edge)
+  const df An1 = zp_shfl(A, G, fwd), Bn1 = zp_shfl(B, G, fwd);
+  // 2. segment totals: the last chunk of a forward segment, the first of a backward one
+  float2* sA = agg;
+  float2* sB = agg + nseg * G;
+  if (fwd ? (ci == cw - 1) : (ci == 0)) {
+    sA[seg * G + col] = make_float2(A.hi, A.lo);
+    sB[seg * G + col] = make_float2(B.hi, B.lo);
+  }
+  __syncthreads();
+  // 3. L: the composition of the segments before this one (forward: segments 0 .. seg-1, applied
+  // in that order; backward: the last segment down to seg+1)
+  df La = df{1.f, 0.f}, Lb = df{0.f, 0.f};
+  for (int t = 0; t < (fwd ? seg : nseg - 1 - seg); t++) {
+    const int j = fwd ? t : nseg - 1 - t;
+    df Aj = zp_f2(sA[j * G + col]), Bj = zp_f2(sB[j * G + col]);
+    zp_compose(Aj, Bj, La, Lb);  // L = Agg_j o L
+    La = Aj;
+    Lb = Bj;
+  }
+  // the carry: the neighbour's output, its segment map applied to L's output (at the segment's
+  // edge, L's output itself)
+  const bool edge = fwd ? (ci == 0) : (ci == cw - 1);
+  return edge ? Lb : An1 * Lb + Bn1;
 }
 
 // The multiplier of row k (table prefix, converged value, last row), as stored (pp_zmul.cuh).
 struct ZpW {
   const float2* wt;
   int wlen, n;
+  bool plus1;  // the table holds w but the thread runs the near -1 form: convert to 1 + w
   df winf, wlast;
   __device__ __forceinline__ df operator()(int k) const {
     if (k == n - 1) return wlast;
-    if (k < wlen) return zp_f2(__ldg(wt + k));
+    if (k < wlen) {
+      const df x = zp_f2(__ldg(wt + k));
+      return plus1 ? x + df{1.f, 0.f} : x;
+    }
     return winf;
   }
 };
@@ -151,7 +191,7 @@ __device__ __forceinline__ void zp_bwd_fix(df (&v)[M], df uin, const ZpW& W, int
 
 template <class S, int M>
 __global__ void __launch_bounds__(512) k_zpart(const ZArgs a, int G, int lgG, int P) {
-  extern __shared__ float2 zp_sm[];  // 2 G P (hi, lo) pairs
+  __shared__ float2 zp_sm[2 * kZpAgg];  // segment totals of the forward and the backward carries
   const int tid = (int)threadIdx.x;
   const int col = tid & (G - 1);
   const int c = tid >> lgG;
@@ -179,13 +219,20 @@ __global__ void __launch_bounds__(512) k_zpart(const ZArgs a, int G, int lgG, in
   W.n = n;
   W.winf = df{0.f, 0.f};
   W.wlast = df{0.f, 0.f};
-  bool n1 = false;
+  bool mine = false;
   if (live) {
     W.winf = zp_f2(m->winf);
     W.wlast = zp_f2(m->wlast);
     W.wlen = m->wlen;
     W.wt = a.wtab + m->woff;
-    n1 = (m->flags & ZF_NEAR1) != 0;
+    mine = (m->flags & ZF_NEAR1) != 0;
+  }
+  // a warp runs the near -1 form when any of its modes needs it (the others convert their w)
+  const bool n1 = __any_sync(0xffffffffu, mine);
+  W.plus1 = n1 && !mine;
+  if (W.plus1) {
+    W.winf = W.winf + df{1.f, 0.f};
+    W.wlast = W.wlast + df{1.f, 0.f};
   }
   const int k0 = c * M;
   // a chunk past the multiplier prefix that does not hold the last row uses winf throughout
@@ -204,22 +251,14 @@ __global__ void __launch_bounds__(512) k_zpart(const ZArgs a, int G, int lgG, in
   // forward recurrence: local pass, carries by recursive doubling, fix-up
   df A = df{1.f, 0.f}, B = df{0.f, 0.f};
   ZP_DISPATCH(zp_fwd, v, A, B, W, k0, scale, dmax);
-  zp_scan(A, B, zp_sm, c, col, G, P, +1);
-  float2* sB = zp_sm + G * P;
-  if (inb) sB[c * G + col] = make_float2(B.hi, B.lo);
-  __syncthreads();
-  const df gin = (inb && c > 0) ? zp_f2(sB[(c - 1) * G + col]) : df{0.f, 0.f};
-  __syncthreads();
+  const df gin = zp_carry(A, B, zp_sm, c, col, G, lgG, +1);
   if (inb && c > 0) ZP_DISPATCH(zp_fwd_fix, v, gin, W, k0);
 
   // back substitution: the same three steps from the top of each chunk
   A = df{1.f, 0.f};
   B = df{0.f, 0.f};
   ZP_DISPATCH(zp_bwd, v, A, B, W, k0);
-  zp_scan(A, B, zp_sm, c, col, G, P, -1);
-  if (inb) sB[c * G + col] = make_float2(B.hi, B.lo);
-  __syncthreads();
-  const df uin = (c + 1 < P) ? zp_f2(sB[(c + 1) * G + col]) : df{0.f, 0.f};
+  const df uin = zp_carry(A, B, zp_sm + kZpAgg, c, col, G, lgG, -1);
   if (c + 1 < P) ZP_DISPATCH(zp_bwd_fix, v, uin, W, k0);
   if (live) {
 #pragma unroll
@@ -252,9 +291,8 @@ static cudaError_t launch_zpart_t(const ZArgs& a, cudaStream_t st) {
   if (!zpart_shape(a.nz, M, &G, &lgG, &P)) return cudaErrorInvalidConfiguration;
   const long long grid = (a.nreal + G - 1) / G;
   if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  const size_t smem = 2 * (size_t)G * P * sizeof(float2);
-  const int threads = (G * P + 31) / 32 * 32;  // whole warps (the range report shuffles full warps)
-  k_zpart<S, M><<<(unsigned)grid, threads, smem, st>>>(a, G, lgG, P);
+  const int threads = (G * P + 31) / 32 * 32;  // whole warps (the scans and the range report shuffle)
+  k_zpart<S, M><<<(unsigned)grid, threads, 0, st>>>(a, G, lgG, P);
   return cudaGetLastError();
 }
 

@@ -128,12 +128,20 @@ template <class S, int MODE> struct ZMinBlocks {
 
 template <class S, int MODE, bool N1>
 __device__ __forceinline__ void z_sweeps(const ZArgs& a, const ZMode& m, S* base, long long P, int n, df scale,
-                                         const float2* wt, float& dmax, float& umax) {
-  const df winf = f2df(m.winf), wlast = f2df(m.wlast);
+                                         const float2* wt, bool plus1, float& dmax, float& umax) {
+  // plus1: this mode stores w itself but runs the near -1 form beside a mode of its warp that needs
+  // it; its multipliers are converted to 1 + w on the fly (exact enough away from -1)
+  const df one = df{1.f, 0.f};
+  df winf = f2df(m.winf), wlast = f2df(m.wlast);
+  if (N1 && plus1) { winf = winf + one; wlast = wlast + one; }
   const int wlen = m.wlen;
   auto W = [&](int k) -> df {
     if (k == n - 1) return wlast;
-    if (k < wlen) return f2df(__ldg(wt + k));
+    if (k < wlen) {
+      df x = f2df(__ldg(wt + k));
+      if (N1 && plus1) x = x + one;
+      return x;
+    }
     return winf;
   };
   constexpr int ZU = ZBatch<S>::v;
@@ -255,8 +263,8 @@ __device__ __forceinline__ void z_sweeps(const ZArgs& a, const ZMode& m, S* base
 // sweeps of all other modes keep the register allocation of the plain form
 template <class S, int MODE>
 __device__ __noinline__ void z_sweeps_near1(const ZArgs& a, const ZMode& m, S* base, long long P, int n, df scale,
-                                            const float2* wt, float& dmax, float& umax) {
-  z_sweeps<S, MODE, true>(a, m, base, P, n, scale, wt, dmax, umax);
+                                            const float2* wt, bool plus1, float& dmax, float& umax) {
+  z_sweeps<S, MODE, true>(a, m, base, P, n, scale, wt, plus1, dmax, umax);
 }
 
 template <class S, int MODE>
@@ -280,8 +288,11 @@ __device__ __forceinline__ void z_line(const ZArgs& a, float& dmax, float& umax)
     z_singular<S>(base, P, n, scale, wt, dmax, umax);
     return;
   }
-  if (flags & ZF_NEAR1) z_sweeps_near1<S, MODE>(a, m, base, P, n, scale, wt, dmax, umax);
-  else z_sweeps<S, MODE, false>(a, m, base, P, n, scale, wt, dmax, umax);
+  // a warp runs the near -1 form when any of its modes needs it (the others convert their w): no
+  // warp runs both forms one after the other
+  const bool mine = (flags & ZF_NEAR1) != 0;
+  if (__any_sync(__activemask(), mine)) z_sweeps_near1<S, MODE>(a, m, base, P, n, scale, wt, !mine, dmax, umax);
+  else z_sweeps<S, MODE, false>(a, m, base, P, n, scale, wt, false, dmax, umax);
 }
 
 // Checkpointed sweeps of the double-float spill (FP64-class plans).  The forward sweep leaves the
@@ -294,14 +305,22 @@ __device__ __forceinline__ void z_line(const ZArgs& a, float& dmax, float& umax)
 // Same arithmetic, in the same order, as the two-sweep kernel.
 template <int MODE, bool N1>
 __device__ __forceinline__ void z_sweeps_ck(const ZArgs& a, const ZMode& m, float2* base, float2* ck, long long P,
-                                            long long CP, int n, df scale, const float2* wt, float& dmax,
-                                            float& umax) {
+                                            long long CP, int n, df scale, const float2* wt, bool plus1,
+                                            float& dmax, float& umax) {
   using S = float2;
-  const df winf = f2df(m.winf), wlast = f2df(m.wlast);
+  // plus1: this mode stores w itself but runs the near -1 form beside a mode of its warp that needs
+  // it; its multipliers are converted to 1 + w on the fly (exact enough away from -1)
+  const df one = df{1.f, 0.f};
+  df winf = f2df(m.winf), wlast = f2df(m.wlast);
+  if (N1 && plus1) { winf = winf + one; wlast = wlast + one; }
   const int wlen = m.wlen;
   auto W = [&](int k) -> df {
     if (k == n - 1) return wlast;
-    if (k < wlen) return f2df(__ldg(wt + k));
+    if (k < wlen) {
+      df x = f2df(__ldg(wt + k));
+      if (N1 && plus1) x = x + one;
+      return x;
+    }
     return winf;
   };
   constexpr int ZU = ZBatch<S>::v;
@@ -450,9 +469,9 @@ __device__ __forceinline__ void z_sweeps_ck(const ZArgs& a, const ZMode& m, floa
 
 template <int MODE>
 __device__ __noinline__ void z_sweeps_ck_near1(const ZArgs& a, const ZMode& m, float2* base, float2* ck, long long P,
-                                               long long CP, int n, df scale, const float2* wt, float& dmax,
-                                               float& umax) {
-  z_sweeps_ck<MODE, true>(a, m, base, ck, P, CP, n, scale, wt, dmax, umax);
+                                               long long CP, int n, df scale, const float2* wt, bool plus1,
+                                               float& dmax, float& umax) {
+  z_sweeps_ck<MODE, true>(a, m, base, ck, P, CP, n, scale, wt, plus1, dmax, umax);
 }
 
 template <int MODE>
@@ -476,8 +495,10 @@ __device__ __forceinline__ void z_line_ck(const ZArgs& a, float& dmax, float& um
     z_singular<S>(base, P, n, scale, wt, dmax, umax);
     return;
   }
-  if (m.flags & ZF_NEAR1) z_sweeps_ck_near1<MODE>(a, m, base, ck, P, CP, n, scale, wt, dmax, umax);
-  else z_sweeps_ck<MODE, false>(a, m, base, ck, P, CP, n, scale, wt, dmax, umax);
+  const bool mine = (m.flags & ZF_NEAR1) != 0;
+  if (__any_sync(__activemask(), mine))
+    z_sweeps_ck_near1<MODE>(a, m, base, ck, P, CP, n, scale, wt, !mine, dmax, umax);
+  else z_sweeps_ck<MODE, false>(a, m, base, ck, P, CP, n, scale, wt, false, dmax, umax);
 }
 
 // 4 CTAs of 256 threads per SM (64 registers; the Thomas sweeps spill 56 bytes and run faster than
