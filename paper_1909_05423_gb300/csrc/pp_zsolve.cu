@@ -110,6 +110,21 @@ __device__ __noinline__ void z_singular(S* base, long long P, int n, df scale, c
   }
 }
 
+// Steps of the Thomas recurrences, g_k = (d_k - g_{k-1}) w_k and u_k = g_k - w_k u_{k+1}.  The
+// FP32-spill sweeps (mixed plans) keep their double-float pairs unnormalised: the leading parts are
+// still summed and multiplied exactly and the low part collects the error terms, so a pair stays
+// good to ~2^-44 of its value over the decay length of the slowest modes, while the values they
+// store are rounded to FP32 anyway; the multipliers, which fix the solved matrix, keep all their
+// bits.  The double-float spill (FP64-class plans) normalises every step.
+template <class S, bool N1> __device__ __forceinline__ df zr_fwd(df d, df g, df w) {
+  if constexpr (sizeof(S) == 4 && !N1) return mul_u(add_u(d, -g), w);
+  else return zw_mul<N1>(d - g, w);
+}
+template <class S, bool N1> __device__ __forceinline__ df zr_bwd(df g, df w, df u) {
+  if constexpr (sizeof(S) == 4 && !N1) return add_u(g, -mul_u(w, u));
+  else return zw_sub<N1>(g, w, u);
+}
+
 // Two-sweep kernel: the forward sweep writes the eliminated values over the right-hand sides, the
 // back substitution reads them back.  It runs for the FP32 spill (mixed plans); the double-float
 // spill runs the checkpointed sweeps below, which share its arithmetic.
@@ -162,7 +177,7 @@ __device__ __forceinline__ void z_sweeps(const ZArgs& a, const ZMode& m, S* base
         for (int u = 0; u < ZU; u++) {
           const df d = zscaled(cur[u], scale);
           track(dmax, d.hi);
-          g = zw_mul<N1>(d - g, winf);
+          g = zr_fwd<S, N1>(d, g, winf);
           zput(base + (k0 + u) * P, g);
         }
       } else {
@@ -172,7 +187,7 @@ __device__ __forceinline__ void z_sweeps(const ZArgs& a, const ZMode& m, S* base
           if (k < n) {
             df d = zscaled(cur[u], scale);
             track(dmax, d.hi);
-            g = zw_mul<N1>(d - g, W(k));
+            g = zr_fwd<S, N1>(d, g, W(k));
             if (periodic && k < qlen) y0 = y0 + f2df(__ldg(qt + k)) * d;
             zput(base + k * P, g);
           }
@@ -194,7 +209,7 @@ __device__ __forceinline__ void z_sweeps(const ZArgs& a, const ZMode& m, S* base
       if (ZFast<S, MODE>::v && k0 - ZU + 1 >= wlen && k0 - ZU + 1 >= qlen && k0 < n - 1) {
 #pragma unroll
         for (int t = 0; t < ZU; t++) {
-          u = zw_sub<N1>(zcvt(cur[t]), winf, u);
+          u = zr_bwd<S, N1>(zcvt(cur[t]), winf, u);
           track(umax, u.hi);
           zput(base + (k0 - t) * P, u);
         }
@@ -208,7 +223,7 @@ __device__ __forceinline__ void z_sweeps(const ZArgs& a, const ZMode& m, S* base
         if (k >= 0) {
           const df gk = zcvt(cur[t]);
           if (k == n - 1) u = periodic ? zw_sub<N1>(gk, wlast, c) : gk;
-          else u = zw_sub<N1>(gk, W(k), u);
+          else u = zr_bwd<S, N1>(gk, W(k), u);
           df outv = u;
           if (periodic && k < qlen) outv = u - cg * f2df(__ldg(qt + k));
           track(umax, outv.hi);
