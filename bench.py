@@ -377,6 +377,47 @@ def _zsolver_study(pp, args):
     return out
 
 
+def _proto_tc_dft32(pp, lines=1 << 22, reps=10):
+    """Prototype tensor-core DFT stage (not on the solve path): 32-point complex DFTs of `lines`
+    lines by tcgen05 bf16 slice products (pp_proto_dft32_tc), against the double-float line kernel
+    on 32-point complex lines (the y-forward of an all-periodic 1024 x 32 x 4096 plan), per complex
+    point; plus its accuracy against numpy's FFT on a sample of lines."""
+    import ctypes
+    import numpy as np
+    import torch
+    from paper_1909_05423_gb300 import _lib
+    lib = _lib.load()
+    P = lambda t: ctypes.c_void_p(t.data_ptr())
+    g = torch.Generator(device="cuda")
+    g.manual_seed(SEED)
+    re = torch.empty(lines, 32, dtype=torch.float64, device="cuda").uniform_(-1.0, 1.0, generator=g)
+    im = torch.empty(lines, 32, dtype=torch.float64, device="cuda").uniform_(-1.0, 1.0, generator=g)
+    ore, oim = torch.empty_like(re), torch.empty_like(im)
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    run = lambda: _lib.check(lib.pp_proto_dft32_tc(P(re), P(im), P(ore), P(oim), lines, P(err), None))
+    tc_ms = _events_ms(run, reps)
+    if int(err.item()) != 0:
+        raise RuntimeError("tensor-core DFT prototype: MMA wait limit reached")
+    k = min(lines, 4096)
+    z = re[:k].cpu().numpy() + 1j * im[:k].cpu().numpy()
+    y = ore[:k].cpu().numpy() + 1j * oim[:k].cpu().numpy()
+    ref = np.fft.fft(z, axis=1)
+    rel = float(np.linalg.norm(y - ref) / np.linalg.norm(ref))
+    del re, im, ore, oim
+    shape = (1024, 32, 4096)
+    plan = pp.Plan(shape, "PPPPPP", (1.0, 1.0, 1.0), "f64", options={"autotune": 1})
+    x = torch.empty(shape, dtype=torch.float64, device="cuda").uniform_(-1.0, 1.0, generator=g)
+    u = torch.empty_like(x)
+    _lib.check(lib.pp_run_stage(plan._h, 0, P(x), P(u), None))
+    y_ms = _events_ms(lambda: _lib.check(lib.pp_run_stage(plan._h, 1, P(x), P(u), None)), reps)
+    plan.close()
+    ylines = (4096 // 2 + 1) * 1024
+    tc_ns, df_ns = tc_ms * 1e6 / (lines * 32), y_ms * 1e6 / (ylines * 32)
+    return {"lines": lines, "tc_ms": tc_ms, "tc_ns_per_complex_point": tc_ns, "rel_l2_vs_numpy": rel,
+            "df_line_kernel_ms": y_ms, "df_lines": ylines, "df_ns_per_complex_point": df_ns,
+            "tc_over_df": tc_ns / df_ns, "adopted": False}
+
+
 def _config4(pp, workloads, args):
     """64 independent grids, sides drawn from {32,...,256} per axis and boundary conditions per axis/face,
     U[-1,1] sources; one graph launch per batch (FP64 and FP32 I/O), with autotuned plans and with the
@@ -658,6 +699,7 @@ def run_ours(args):
         variants["config4_batched"] = _config4(pp, workloads, args)
         variants["config5_adjoint"] = _config5(pp, workloads, args)
         variants["zsolver_study_64x64"] = _zsolver_study(pp, args)
+        variants["proto_tc_dft32"] = _proto_tc_dft32(pp)
         u = torch.empty_like(f)
         plan.solve(f, u)
 
@@ -740,9 +782,15 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="fixed launch-shape heuristics instead of the autotuner")
     ap.add_argument("--n3", type=int, nargs="+", default=[512, 1024],
                     help="grid sides of the config-3 mixed-precision variant")
+    ap.add_argument("--proto-tc", type=int, default=0, metavar="LINES",
+                    help="time only the tensor-core DFT prototype on LINES lines (profiling captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.proto_tc:
+        import paper_1909_05423_gb300 as pp
+        print(json.dumps({"proto_tc_dft32": _proto_tc_dft32(pp, args.proto_tc, max(args.steps, 1))}))
+        return 0
     return run_ours(args)
 
 

@@ -253,6 +253,30 @@ pp_status pp_plan_z_method(const pp_plan* plan, int* out);
  * by options.z_split or the autotuner; periodic z reports 1.  Errors: PP_ERR_INVALID_ARG (NULL). */
 pp_status pp_plan_z_split(const pp_plan* plan, int* out);
 
+/* ---- Prototype, not used by the solver: a DFT stage on the tensor cores (tcgen05, TMEM). ----
+ * Measures whether a small-radix DFT stage posed as a dense product beats the double-float FFT stage
+ * (Sec. "Computational Complexity Analysis" counts the transforms as the dominant work).
+ *
+ * pp_proto_tc_gemm_check: D = A B^T for A 128 x 64 and B 64 x 64 (bf16 bit patterns, row-major,
+ * device), D 128 x 64 FP32 (device), by one CTA with four tcgen05.mma; swap = 1 exchanges the two
+ * core-matrix offsets in the shared-memory descriptors (a self-check of the operand layout: only one
+ * order reproduces A B^T).  *err_dev (device int, zeroed by the caller) becomes 1 if the MMAs did not
+ * complete within the kernel's wait limit.  Asynchronous on stream.  Errors: PP_ERR_INVALID_ARG
+ * (NULL), PP_ERR_CUDA (launch). */
+pp_status pp_proto_tc_gemm_check(const void* A_dev, const void* B_dev, void* D_dev, int swap, int* err_dev,
+                                 pp_stream_t stream);
+
+/* pp_proto_dft32_tc: forward DFTs Y_k = sum_n z_n exp(-2 pi i n k / 32) of `lines` lines of 32
+ * complex points (re_dev, im_dev: FP64 [lines][32], device; outputs the same, not aliasing the
+ * inputs), at double-float accuracy from bf16 products: every line scaled by a power of two and cut
+ * into seven 7-bit slices, the 28 slice products of the levels kept accumulated exactly in FP32
+ * tensor memory, the levels summed in double-float (Ozaki-style splitting).  The seven slices of
+ * the real 64 x 64 DFT matrix are built on the host and kept on the device (first call per device,
+ * synchronous).  *err_dev as above.  Asynchronous on stream otherwise.  Errors:
+ * PP_ERR_INVALID_ARG (NULL, lines < 0), PP_ERR_OUT_OF_MEMORY (the table), PP_ERR_CUDA (launch). */
+pp_status pp_proto_dft32_tc(const double* re_dev, const double* im_dev, double* out_re_dev, double* out_im_dev,
+                            long long lines, int* err_dev, pp_stream_t stream);
+
 /* Human-readable detail of the last error on the calling thread ("" if none). */
 const char* pp_last_error_string(void);
 

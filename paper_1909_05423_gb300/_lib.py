@@ -23,7 +23,7 @@ DTYPES = {"f64": 0, "mixed_f64io": 1, "mixed_f32io": 2}
 # every entry point declared in include/pittpack_gb.h
 EXPORTS = ["pp_plan_create", "pp_solve", "pp_solve_refined", "pp_solve_refined_noalloc", "pp_fold_bc", "pp_solve_batched",
            "pp_solve_adjoint", "pp_solve_host", "pp_run_stage", "pp_plan_destroy", "pp_plan_status", "pp_plan_device_bytes",
-           "pp_plan_launch_shapes", "pp_plan_z_method", "pp_plan_z_split", "pp_last_error_string", "pp_version"]
+           "pp_plan_launch_shapes", "pp_plan_z_method", "pp_plan_z_split", "pp_proto_tc_gemm_check", "pp_proto_dft32_tc", "pp_last_error_string", "pp_version"]
 
 
 class PPError(RuntimeError):
@@ -81,6 +81,10 @@ def load():
         lib.pp_plan_z_method.restype = ctypes.c_int
         lib.pp_plan_z_split.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
         lib.pp_plan_z_split.restype = ctypes.c_int
+        lib.pp_proto_tc_gemm_check.argtypes = [vp, vp, vp, ctypes.c_int, vp, vp]
+        lib.pp_proto_tc_gemm_check.restype = ctypes.c_int
+        lib.pp_proto_dft32_tc.argtypes = [vp, vp, vp, vp, ctypes.c_longlong, vp, vp]
+        lib.pp_proto_dft32_tc.restype = ctypes.c_int
         lib.pp_last_error_string.argtypes = []
         lib.pp_last_error_string.restype = ctypes.c_char_p
         lib.pp_version.argtypes = []
