@@ -119,18 +119,23 @@ struct ZpW {
   }
 };
 
-// The four passes over a thread's M rows (FAST: every row past the table prefix and not the last
-// row, so w = winf throughout).  No barrier inside: a CTA's threads may take different variants.
+// chunks of 16 rows keep their multipliers in registers across the four passes (measured: at 8 rows
+// the extra registers halve the resident CTAs, at 32 they spill)
+template <int M> struct ZpCacheW { static constexpr bool v = M == 16; };
+
+// The four passes over a thread's M rows, with the chunk's multipliers wv loaded once (FAST: every
+// row past the table prefix and not the last row, so w = winf throughout and wv is not read).  No
+// barrier inside: a CTA's threads may take different variants.
 // 1. forward recurrence from a zero carry: v = local g, (A, B) = the chunk's map
 template <int M, bool N1, bool FAST>
-__device__ __forceinline__ void zp_fwd(df (&v)[M], df& A, df& B, const ZpW& W, int k0, df scale, float& dmax) {
+__device__ __forceinline__ void zp_fwd(df (&v)[M], df& A, df& B, const ZpW& W, const df (&wv)[M], int k0, df scale, float& dmax) {
 #pragma unroll
   for (int i = 0; i < M; i++) {
     const int k = k0 + i;
     if (FAST || k < W.n) {
       const df d = v[i] * scale;
       track(dmax, d.hi);
-      const df w = FAST ? W.winf : W(k);
+      const df w = FAST ? W.winf : (ZpCacheW<M>::v ? wv[i] : W(k));
       B = zw_mul<N1>(d - B, w);
       A = zw_neg_mul<N1>(A, w);
       v[i] = B;
@@ -139,25 +144,25 @@ __device__ __forceinline__ void zp_fwd(df (&v)[M], df& A, df& B, const ZpW& W, i
 }
 // 2. g_k = local g_k + (a_k0 ... a_k) g_in
 template <int M, bool N1, bool FAST>
-__device__ __forceinline__ void zp_fwd_fix(df (&v)[M], df gin, const ZpW& W, int k0) {
+__device__ __forceinline__ void zp_fwd_fix(df (&v)[M], df gin, const ZpW& W, const df (&wv)[M], int k0) {
   df Pk = df{1.f, 0.f};
 #pragma unroll
   for (int i = 0; i < M; i++) {
     const int k = k0 + i;
     if (FAST || k < W.n) {
-      Pk = zw_neg_mul<N1>(Pk, FAST ? W.winf : W(k));
+      Pk = zw_neg_mul<N1>(Pk, FAST ? W.winf : (ZpCacheW<M>::v ? wv[i] : W(k)));
       v[i] = v[i] + Pk * gin;
     }
   }
 }
 // 3. back substitution u_k = g_k - w_k u_{k+1} from a zero carry above the chunk
 template <int M, bool N1, bool FAST>
-__device__ __forceinline__ void zp_bwd(df (&v)[M], df& A, df& B, const ZpW& W, int k0) {
+__device__ __forceinline__ void zp_bwd(df (&v)[M], df& A, df& B, const ZpW& W, const df (&wv)[M], int k0) {
 #pragma unroll
   for (int i = M - 1; i >= 0; i--) {
     const int k = k0 + i;
     if (FAST || k < W.n) {
-      const df w = FAST ? W.winf : W(k);
+      const df w = FAST ? W.winf : (ZpCacheW<M>::v ? wv[i] : W(k));
       B = zw_sub<N1>(v[i], w, B);
       A = zw_neg_mul<N1>(A, w);
       v[i] = B;
@@ -166,13 +171,13 @@ __device__ __forceinline__ void zp_bwd(df (&v)[M], df& A, df& B, const ZpW& W, i
 }
 // 4. u_k = local u_k + (a_k ... a_end) u_in
 template <int M, bool N1, bool FAST>
-__device__ __forceinline__ void zp_bwd_fix(df (&v)[M], df uin, const ZpW& W, int k0) {
+__device__ __forceinline__ void zp_bwd_fix(df (&v)[M], df uin, const ZpW& W, const df (&wv)[M], int k0) {
   df Qk = df{1.f, 0.f};
 #pragma unroll
   for (int i = M - 1; i >= 0; i--) {
     const int k = k0 + i;
     if (FAST || k < W.n) {
-      Qk = zw_neg_mul<N1>(Qk, FAST ? W.winf : W(k));
+      Qk = zw_neg_mul<N1>(Qk, FAST ? W.winf : (ZpCacheW<M>::v ? wv[i] : W(k)));
       v[i] = v[i] + Qk * uin;
     }
   }
@@ -240,6 +245,10 @@ __global__ void __launch_bounds__(512) k_zpart(const ZArgs a, int G, int lgG, in
   const df scale = df{a.scale[0], a.scale[1]};
   S* base = reinterpret_cast<S*>(a.data) + s;
   float dmax = 0.0f, umax = 0.0f;
+  // the chunk's multipliers, loaded once for the four passes (chunks in the table prefix)
+  df wv[M];
+#pragma unroll
+  for (int i = 0; i < M; i++) wv[i] = (ZpCacheW<M>::v && !fast && k0 + i < n) ? W(k0 + i) : W.winf;
 
   df v[M];
 #pragma unroll
@@ -250,16 +259,16 @@ __global__ void __launch_bounds__(512) k_zpart(const ZArgs a, int G, int lgG, in
 
   // forward recurrence: local pass, carries by recursive doubling, fix-up
   df A = df{1.f, 0.f}, B = df{0.f, 0.f};
-  ZP_DISPATCH(zp_fwd, v, A, B, W, k0, scale, dmax);
+  ZP_DISPATCH(zp_fwd, v, A, B, W, wv, k0, scale, dmax);
   const df gin = zp_carry(A, B, zp_sm, c, col, G, lgG, +1);
-  if (inb && c > 0) ZP_DISPATCH(zp_fwd_fix, v, gin, W, k0);
+  if (inb && c > 0) ZP_DISPATCH(zp_fwd_fix, v, gin, W, wv, k0);
 
   // back substitution: the same three steps from the top of each chunk
   A = df{1.f, 0.f};
   B = df{0.f, 0.f};
-  ZP_DISPATCH(zp_bwd, v, A, B, W, k0);
+  ZP_DISPATCH(zp_bwd, v, A, B, W, wv, k0);
   const df uin = zp_carry(A, B, zp_sm + kZpAgg, c, col, G, lgG, -1);
-  if (c + 1 < P) ZP_DISPATCH(zp_bwd_fix, v, uin, W, k0);
+  if (c + 1 < P) ZP_DISPATCH(zp_bwd_fix, v, uin, W, wv, k0);
   if (live) {
 #pragma unroll
     for (int i = 0; i < M; i++) {
