@@ -1005,9 +1005,22 @@ struct BatchGraph {
 std::mutex g_batch_mu;
 std::vector<BatchGraph> g_batch_cache;  // most recent last
 constexpr size_t kBatchCacheMax = 8;
+// Settings chosen for a list of plans (see tune_batch): 0 = every member's own, 1 = the shared-GPU
+// settings for its autotuned members.  Kept while all of the plans live.
+struct BatchChoice {
+  std::vector<const pp_plan*> plans;
+  int choice;
+};
+std::vector<BatchChoice> g_batch_choice;
+constexpr size_t kBatchChoiceMax = 64;
 
 void evict_plan(const pp_plan* p) {
   std::lock_guard<std::mutex> lk(g_batch_mu);
+  for (size_t i = 0; i < g_batch_choice.size();) {
+    const auto& v = g_batch_choice[i].plans;
+    if (std::find(v.begin(), v.end(), p) != v.end()) g_batch_choice.erase(g_batch_choice.begin() + i);
+    else i++;
+  }
   for (size_t i = 0; i < g_batch_cache.size();) {
     const auto& k = g_batch_cache[i].key;
     size_t n = k.size() / 3;
@@ -1022,6 +1035,174 @@ void evict_plan(const pp_plan* p) {
   }
 }
 }  // namespace
+
+// Launch settings of a plan that a batched graph may swap: launch shapes and the z split.
+struct PlanSettings {
+  int threads_x[2], lpc_x[2], ldm_x, threads_y[2], lpc_y[2], ldm_y, threads_z, lpc_z, ldm_z, zsplit;
+};
+static PlanSettings get_settings(const pp_plan* p) {
+  PlanSettings s;
+  for (int d = 0; d < 2; d++) {
+    s.threads_x[d] = p->threads_x[d]; s.lpc_x[d] = p->lpc_x[d];
+    s.threads_y[d] = p->threads_y[d]; s.lpc_y[d] = p->lpc_y[d];
+  }
+  s.ldm_x = p->ldm_x; s.ldm_y = p->ldm_y;
+  s.threads_z = p->threads_z; s.lpc_z = p->lpc_z; s.ldm_z = p->ldm_z;
+  s.zsplit = p->zsplit;
+  return s;
+}
+static void set_settings(pp_plan* p, const PlanSettings& s) {
+  for (int d = 0; d < 2; d++) {
+    p->threads_x[d] = s.threads_x[d]; p->lpc_x[d] = s.lpc_x[d];
+    p->threads_y[d] = s.threads_y[d]; p->lpc_y[d] = s.lpc_y[d];
+  }
+  p->ldm_x = s.ldm_x; p->ldm_y = s.ldm_y;
+  p->threads_z = s.threads_z; p->lpc_z = s.lpc_z; p->ldm_z = s.ldm_z;
+  p->zsplit = s.zsplit;
+}
+
+// Puts the autotuned members of a batch on the library's shared-GPU settings -- the default launch
+// shapes and, where the autotuner chose the z split, the Thomas sweeps -- for the scope of one
+// capture, and restores their own settings afterwards (a captured graph keeps the launch
+// parameters it was captured with).
+struct SettingsSwap {
+  std::vector<std::pair<pp_plan*, PlanSettings>> saved;
+  void apply(pp_plan* const* plans, int n) {
+    for (int i = 0; i < n; i++) {
+      pp_plan* p = plans[i];
+      if (!p->tuned) continue;
+      bool seen = false;
+      for (const auto& s : saved) seen |= (s.first == p);
+      if (seen) continue;
+      saved.emplace_back(p, get_settings(p));
+      choose_shapes(p, nullptr);
+      if (p->zsplit_tuned) p->zsplit = 1;
+    }
+  }
+  ~SettingsSwap() {
+    for (const auto& s : saved) set_settings(s.first, s.second);
+  }
+};
+
+// Capture the batch on private streams: a fork event fans the members out over up to
+// kBranches capture streams (members that share a plan stay on one branch, in order, since
+// they share its workspace), a join brings them back; the graph's branches run concurrently.
+static pp_status capture_batch(pp_plan* const* plans, const void* const* f, void* const* u, int n,
+                               cudaGraphExec_t* out) {
+  constexpr int kBranches = 32;
+  std::vector<const pp_plan*> uniq;
+  std::vector<int> branch(n);
+  for (int i = 0; i < n; i++) {
+    int b = -1;
+    for (size_t j = 0; j < uniq.size(); j++)
+      if (uniq[j] == plans[i]) { b = (int)(j % kBranches); break; }
+    if (b < 0) { b = (int)(uniq.size() % kBranches); uniq.push_back(plans[i]); }
+    branch[i] = b;
+  }
+  const int nb = (int)std::min<size_t>(uniq.size(), kBranches);
+  cudaStream_t cap;
+  CUDA_OK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  std::vector<cudaStream_t> br(nb, nullptr);
+  std::vector<cudaEvent_t> ev(nb + 1, nullptr);
+  cudaError_t e = cudaSuccess;
+  for (int b = 0; b < nb && e == cudaSuccess; b++) e = cudaStreamCreateWithFlags(&br[b], cudaStreamNonBlocking);
+  for (int b = 0; b <= nb && e == cudaSuccess; b++) e = cudaEventCreateWithFlags(&ev[b], cudaEventDisableTiming);
+  auto cleanup = [&]() {
+    for (cudaStream_t x : br) if (x) cudaStreamDestroy(x);
+    for (cudaEvent_t x : ev) if (x) cudaEventDestroy(x);
+    cudaStreamDestroy(cap);
+  };
+  if (e != cudaSuccess) { cleanup(); return fail(PP_ERR_CUDA, "batch streams/events: %s", cudaGetErrorString(e)); }
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) {
+    cleanup();
+    return fail(PP_ERR_CUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
+  }
+  pp_status s = PP_OK;
+  e = cudaEventRecord(ev[nb], cap);
+  for (int b = 0; b < nb && e == cudaSuccess; b++) e = cudaStreamWaitEvent(br[b], ev[nb], 0);
+  if (e != cudaSuccess) s = fail(PP_ERR_CUDA, "batch fork: %s", cudaGetErrorString(e));
+  for (int i = 0; i < n && s == PP_OK; i++) s = run_pipeline(plans[i], f[i], u[i], 0, br[branch[i]]);
+  for (int b = 0; b < nb; b++) {
+    cudaEventRecord(ev[b], br[b]);
+    cudaStreamWaitEvent(cap, ev[b], 0);
+  }
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(cap, &graph);
+  cleanup();
+  if (s != PP_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (e != cudaSuccess) return fail(PP_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+  cudaGraphExec_t exec = nullptr;
+  e = inject("graph") ? cudaErrorInvalidValue : cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(PP_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+  *out = exec;
+  return PP_OK;
+}
+
+// Shortest of three replays of an executable graph on st (after one warm-up), ms; +inf on error.
+static float time_graph(cudaGraphExec_t g, cudaStream_t st) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  float best = 1e30f;
+  if (cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess && cudaGraphLaunch(g, st) == cudaSuccess) {
+    for (int r = 0; r < 3; r++) {
+      if (cudaEventRecord(a, st) != cudaSuccess || cudaGraphLaunch(g, st) != cudaSuccess ||
+          cudaEventRecord(b, st) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess)
+        break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      best = std::min(best, ms);
+    }
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  return best;
+}
+
+// An autotuned plan carries the settings that were fastest for it alone on the GPU (autotune): for a
+// plan with few modes that is often the partitioned z solve and small tiles, which buy latency with
+// extra work.  In a batch graph the members share the GPU and throughput decides, so the first batch
+// over a list of plans with autotuned members times its graph twice on scratch buffers of the
+// members' sizes -- with every member's own settings, and with the shared-GPU settings for the
+// autotuned ones (SettingsSwap) -- and returns which was faster (0 own, 1 shared).  It waits for
+// earlier work on st, which may still use the members' workspaces, and allocates the scratch for
+// the duration of the call; without the memory it keeps the members' own settings.
+static int tune_batch(pp_plan* const* plans, int n, cudaStream_t st) {
+  if (cudaStreamSynchronize(st) != cudaSuccess) return 0;
+  std::vector<void*> fs(n, nullptr), us(n, nullptr);
+  bool ok = true;
+  for (int i = 0; i < n && ok; i++) {
+    const bool f32 = (plans[i]->dtype == PP_MIXED_F32IO);
+    const long long pts = (long long)plans[i]->nx * plans[i]->ny * plans[i]->nz;
+    const size_t bytes = (size_t)pts * (f32 ? 4 : 8);
+    ok = cudaMalloc(&fs[i], bytes) == cudaSuccess && cudaMalloc(&us[i], bytes) == cudaSuccess &&
+         launch_fill(fs[i], pts, f32, st) == cudaSuccess;
+  }
+  int choice = 0;
+  if (ok) {
+    float t[2] = {1e30f, 1e30f};
+    for (int v = 0; v < 2; v++) {
+      SettingsSwap swap;
+      if (v == 1) swap.apply(plans, n);
+      cudaGraphExec_t g = nullptr;
+      if (capture_batch(plans, fs.data(), us.data(), n, &g) == PP_OK) {
+        t[v] = time_graph(g, st);
+        cudaGraphExecDestroy(g);
+      }
+    }
+    choice = (t[1] < t[0]) ? 1 : 0;
+  }
+  cudaStreamSynchronize(st);
+  for (void* x : fs) if (x) cudaFree(x);
+  for (void* x : us) if (x) cudaFree(x);
+  (void)cudaGetLastError();  // a failed timing run leaves nothing for the caller's launches
+  // the timing runs' status (scratch data) is not the caller's
+  for (int i = 0; i < n; i++) cudaMemset(plans[i]->d_status, 0, sizeof(unsigned));
+  return choice;
+}
 
 // ------------------------------------------------------------------ C ABI
 extern "C" {
@@ -1130,6 +1311,8 @@ pp_status pp_plan_create(pp_plan** out, int nx, int ny, int nz, const pp_bc bc[6
   if (opt && opt->autotune) {
     pp_status ts = autotune(p, zreq == 0, sreq == 0 && !zper);
     if (ts != PP_OK) { free_plan(p); return ts; }
+    p->tuned = true;
+    p->zsplit_tuned = (sreq == 0 && !zper);
   }
   *out = p;
   return PP_OK;
@@ -1217,60 +1400,34 @@ pp_status pp_solve_batched(pp_plan* const* plans, const void* const* f, void* co
       }
     }
   }
-  // Capture the batch on private streams: a fork event fans the members out over up to
-  // kBranches capture streams (members that share a plan stay on one branch, in order, since
-  // they share its workspace), a join brings them back; the graph's branches run concurrently.
-  constexpr int kBranches = 32;
-  std::vector<const pp_plan*> uniq;
-  std::vector<int> branch(n);
-  for (int i = 0; i < n; i++) {
-    int b = -1;
-    for (size_t j = 0; j < uniq.size(); j++)
-      if (uniq[j] == plans[i]) { b = (int)(j % kBranches); break; }
-    if (b < 0) { b = (int)(uniq.size() % kBranches); uniq.push_back(plans[i]); }
-    branch[i] = b;
+  // Launch settings of the batch: tuned once per list of plans that includes autotuned members.
+  int choice = 0;
+  bool any_tuned = false;
+  for (int i = 0; i < n; i++) any_tuned |= plans[i]->tuned;
+  if (any_tuned) {
+    const std::vector<const pp_plan*> pk(plans, plans + n);
+    bool found = false;
+    {
+      std::lock_guard<std::mutex> lk(g_batch_mu);
+      for (const BatchChoice& c : g_batch_choice)
+        if (c.plans == pk) { choice = c.choice; found = true; break; }
+    }
+    if (!found) {
+      choice = tune_batch(plans, n, st);
+      std::lock_guard<std::mutex> lk(g_batch_mu);
+      if (g_batch_choice.size() >= kBatchChoiceMax) g_batch_choice.erase(g_batch_choice.begin());
+      g_batch_choice.push_back(BatchChoice{pk, choice});
+    }
   }
-  const int nb = (int)std::min<size_t>(uniq.size(), kBranches);
-  cudaStream_t cap;
-  CUDA_OK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-  std::vector<cudaStream_t> br(nb, nullptr);
-  std::vector<cudaEvent_t> ev(nb + 1, nullptr);
-  cudaError_t e = cudaSuccess;
-  for (int b = 0; b < nb && e == cudaSuccess; b++) e = cudaStreamCreateWithFlags(&br[b], cudaStreamNonBlocking);
-  for (int b = 0; b <= nb && e == cudaSuccess; b++) e = cudaEventCreateWithFlags(&ev[b], cudaEventDisableTiming);
-  auto cleanup = [&]() {
-    for (cudaStream_t x : br) if (x) cudaStreamDestroy(x);
-    for (cudaEvent_t x : ev) if (x) cudaEventDestroy(x);
-    cudaStreamDestroy(cap);
-  };
-  if (e != cudaSuccess) { cleanup(); return fail(PP_ERR_CUDA, "batch streams/events: %s", cudaGetErrorString(e)); }
-  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
-  if (e != cudaSuccess) {
-    cleanup();
-    return fail(PP_ERR_CUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
-  }
-  pp_status s = PP_OK;
-  e = cudaEventRecord(ev[nb], cap);
-  for (int b = 0; b < nb && e == cudaSuccess; b++) e = cudaStreamWaitEvent(br[b], ev[nb], 0);
-  if (e != cudaSuccess) s = fail(PP_ERR_CUDA, "batch fork: %s", cudaGetErrorString(e));
-  for (int i = 0; i < n && s == PP_OK; i++) s = run_pipeline(plans[i], f[i], u[i], 0, br[branch[i]]);
-  for (int b = 0; b < nb; b++) {
-    cudaEventRecord(ev[b], br[b]);
-    cudaStreamWaitEvent(cap, ev[b], 0);
-  }
-  cudaGraph_t graph = nullptr;
-  e = cudaStreamEndCapture(cap, &graph);
-  cleanup();
-  if (s != PP_OK) {
-    if (graph) cudaGraphDestroy(graph);
-    return s;
-  }
-  if (e != cudaSuccess) return fail(PP_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
   cudaGraphExec_t exec = nullptr;
-  e = inject("graph") ? cudaErrorInvalidValue : cudaGraphInstantiate(&exec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e != cudaSuccess) return fail(PP_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
-  e = cudaGraphLaunch(exec, st);
+  pp_status s;
+  {
+    SettingsSwap swap;
+    if (choice == 1) swap.apply(plans, n);
+    s = capture_batch(plans, f, u, n, &exec);
+  }
+  if (s != PP_OK) return s;
+  cudaError_t e = cudaGraphLaunch(exec, st);
   if (e != cudaSuccess) {
     cudaGraphExecDestroy(exec);
     return fail(PP_ERR_CUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));

@@ -297,6 +297,47 @@ def test_batched_config4_shaped(oracle, dtype):
         p.close()
 
 
+@pytest.mark.parametrize("dtype", ["f64", "mixed_f32io"])
+def test_batched_autotuned_members(oracle, dtype):
+    """A batch whose members were autotuned: its first call times the graph with the members' own
+    settings and with the shared-GPU settings, and keeps the faster.  Every member still matches the
+    oracle (first call and replay with new data), a member may appear twice and beside a plan with
+    default settings, and the plans' own launch shapes and z split are unchanged afterwards, for
+    their lone solves."""
+    import paper_1909_05423_gb300 as pp
+    grids = [g for g in workloads.batched_grids(seed=7, count=10, sides=(12, 18, 24, 32, 36, 48))]
+    io = torch.float32 if dtype == "mixed_f32io" else torch.float64
+    tol = TOL_F64 if dtype == "f64" else 1e-6
+    sps = [(1.0 / s[2], 1.0 / s[1], 1.0 / s[0]) for s, _ in grids]
+    plans = [pp.Plan(s, bc, sp, dtype, options={"autotune": 1} if i else None)
+             for i, ((s, bc), sp) in enumerate(zip(grids, sps))]
+    plans.append(plans[3])
+    grids.append(grids[3])
+    sps.append(sps[3])
+    before = [(p.launch_shapes(), p.z_split()) for p in plans]
+    fs = [torch.empty(s, dtype=io, device="cuda") for s, _ in grids]
+    us = [torch.empty_like(f) for f in fs]
+    for rep in range(2):
+        host = [workloads.uniform_source(s, seed=700 + 20 * rep + i) for i, (s, _) in enumerate(grids)]
+        for f, h in zip(fs, host):
+            f.copy_(torch.from_numpy(h))
+        pp.solve_batched(plans, fs, us)
+        torch.cuda.synchronize()
+        for (s, bc), sp, h, u in zip(grids, sps, host, us):
+            ref = oracle.solve(h.astype(np.float32).astype(np.float64) if dtype == "mixed_f32io" else h, bc, sp)
+            assert rel_l2(u.double().cpu().numpy(), ref) <= tol
+    assert [(p.launch_shapes(), p.z_split()) for p in plans] == before
+    # a lone solve after the batch runs with the plan's own settings
+    s, bc = grids[1]
+    h = workloads.uniform_source(s, seed=799)
+    u = plans[1].solve(torch.from_numpy(h).to(device="cuda", dtype=io))
+    torch.cuda.synchronize()
+    ref = oracle.solve(h.astype(np.float32).astype(np.float64) if dtype == "mixed_f32io" else h, bc, sps[1])
+    assert rel_l2(u.double().cpu().numpy(), ref) <= tol
+    for p in plans[:-1]:
+        p.close()
+
+
 def test_autotuned_plan_matches_oracle(oracle):
     """A plan created with autotune=1 (launch shapes timed and chosen at creation, then cached)
     gives the same parity as the default shapes."""
