@@ -420,9 +420,9 @@ def _proto_tc_dft32(pp, lines=1 << 22, reps=10):
 
 def _config4(pp, workloads, args):
     """64 independent grids, sides drawn from {32,...,256} per axis and boundary conditions per axis/face,
-    U[-1,1] sources; one graph launch per batch (FP64 and FP32 I/O), with autotuned plans and with the
-    heuristic launch shapes (the autotuner times each stage alone or as concurrent copies of itself;
-    inside the batch graph the FP64 members ran faster with the heuristic shapes, measured)."""
+    U[-1,1] sources; one graph launch per batch (FP64 and FP32 I/O), with autotuned plans (each plan
+    tuned alone at creation, then the batch graph tuned as a whole on its first call) and with the
+    default launch shapes."""
     import torch
     grids = workloads.batched_grids(seed=4, count=64)
     pts = sum(s[0] * s[1] * s[2] for s, _ in grids)

@@ -178,8 +178,16 @@ pp_status pp_fold_bc(pp_plan* plan, const void* f_in, void* f_out, const void* c
  * batches are cached; pp_plan_destroy evicts the graphs that use that plan).  Members run on
  * up to 32 concurrent graph branches (measured: 8 -> 32 took 64 uneven grids from 4.19 to 4.04 ms
  * FP64, 2.26 to 2.13 ms FP32); members that share a plan share its workspace and run
- * one after another on one branch.  Errors: PP_ERR_INVALID_ARG (n < 0, NULL arrays or
- * members), PP_ERR_CUDA (capture/instantiate/launch). */
+ * one after another on one branch.
+ * Autotuned members (options.autotune = 1) carry the settings that were fastest for each plan
+ * alone, which in a shared graph can lose to the default ones (measured: 64 uneven grids, 5.36
+ * against 4.30 ms FP64).  So the first call over a list of plans that includes autotuned members
+ * waits for `stream` to be idle, allocates scratch grids of the members' sizes for the duration
+ * of the call, and times the graph with the members' own settings and with the default launch
+ * shapes and Thomas sweeps for the autotuned members; the faster is kept for that list of plans
+ * (the plans themselves keep their settings for pp_solve).  Without the scratch memory the
+ * members' own settings are used.  Errors: PP_ERR_INVALID_ARG (n < 0, NULL arrays or members),
+ * PP_ERR_CUDA (capture/instantiate/launch). */
 pp_status pp_solve_batched(pp_plan* const* plans, const void* const* f, void* const* u, int n,
                            pp_stream_t stream);
 
