@@ -127,16 +127,17 @@ pp_status pp_solve(pp_plan* plan, const void* f_dev, void* u_dev, pp_stream_t st
  * FP32), r = f - A u0 (7-point stencil of Sec. "Mathematical Formulation"; the second
  * differences of u0 are formed exactly, then scaled by 1/h^2 and subtracted from f in double-float
  * arithmetic, so r is accurate to ~2^-46 |f|), delta = solve(r) with FP32 I/O, u = u0 + delta
- * (rounded once to FP64).  The error of u is about the square of the mixed solve's (~1e-13 against
- * the exact discrete solution).  Only for PP_MIXED_F64IO plans (PP_ERR_INVALID_ARG otherwise).  u
+ * (rounded once to FP64).  Measured against the exact discrete solution of manufactured problems:
+ * 1e-13 to 6e-13 at 64^3, 2.5e-12 to 3.2e-12 at 512^3, 5e-12 to 6e-12 at 1024^3 (one step multiplies
+ * the mixed error by the correction solve's relative accuracy, ~1e-6).  Only for PP_MIXED_F64IO plans (PP_ERR_INVALID_ARG otherwise).  u
  * must not alias f.  The first call on a plan allocates its scratch: u0 and r in FP32, 8 bytes per
  * cell. */
 pp_status pp_solve_refined(pp_plan* plan, const void* f_dev, void* u_dev, pp_stream_t stream);
 
 /* pp_solve_refined without any device allocation.  (The paper has no counterpart: it is an
- * addition for callers that cannot allocate device memory when they solve -- code running
- * while a stream is captured into a CUDA graph, where cudaMalloc is refused; time-stepping
- * loops that must not allocate mid-run; applications whose own allocator owns the GPU.)
+ * addition for callers that cannot allocate device memory when they solve -- time-stepping
+ * loops that must not allocate, or risk an out-of-memory error, in the middle of a run, and
+ * applications whose own memory manager has reserved the GPU's memory.)
  * pp_solve_refined allocates a grid-sized residual buffer on its first call; this entry point
  * instead uses a fixed 16 MiB device array inside the library (held by every GPU that loads the
  * library until the process exits) plus the plan's own workspace.  Same arithmetic as

@@ -2,10 +2,9 @@
 //
 // pp_solve_refined() allocates, on its first call on a plan, a grid-sized buffer for the
 // residual / correction and a small buffer for the partial sums of the mean.  Some callers
-// cannot allocate at that point: code that runs while a stream is being captured into a CUDA
-// graph (cudaMalloc is not a stream operation and is refused in that mode), time-stepping
-// loops that must not allocate or risk an out-of-memory error mid-run, and host applications
-// whose own memory manager owns the device memory.  pp_solve_refined_noalloc() gives them the
+// cannot allocate at that point: time-stepping loops that must not allocate or risk an
+// out-of-memory error mid-run, and host applications whose own memory manager owns the device
+// memory.  pp_solve_refined_noalloc() gives them the
 // same result with no allocation at all: its scratch is the file-scope device array below,
 // which every GPU that loads this library holds until the process exits.
 #include <cstdio>

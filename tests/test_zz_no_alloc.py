@@ -1,5 +1,5 @@
 """pp_solve_refined_noalloc: the refined mixed-precision solve for callers that cannot allocate
-device memory when they solve (stream capture, allocation-free time loops, host-owned memory).
+device memory when they solve (allocation-free time loops, memory owned by the host application).
 It must give the same result as pp_solve_refined, call after call, through the C ABI.
 
 This file is collected last on purpose: it also checks that the library's shared scratch array
