@@ -10,6 +10,8 @@
 // place; the host sizes the batch so that a stage never needs more than NB(r)
 // butterflies per thread.
 #pragma once
+#include <type_traits>
+
 #include "pp_arith.cuh"
 
 namespace pp {
@@ -319,15 +321,30 @@ __device__ __forceinline__ void fft_stage_ct(cx<R>* buf, int nlines, int ldm, co
     constexpr int TPL = MC / VPT;
     constexpr int NB = nbl / TPL;  // butterflies per thread
     static_assert(NB * TPL == nbl && NB * RAD <= 16, "team covers the line");
+    // FP32 lines of 512 points (radix 8, 8, 8): the first stage writes its output transposed, as an
+    // 8 x 64 array (output 8p + t at 64t + p), and the second stage reads it so.  The first stage's
+    // stores are then consecutive across a warp instead of 64 bytes apart (a two-way bank conflict
+    // on every one of its 8-byte stores), and with the one-in-32 padding the second stage's loads
+    // stay conflict-free and at compile-time offsets: pad(64a + b + 8u) = 66a + b + 8u + (8u >> 5)
+    // for a = j mod 8, b = j / 8 < 8.
+    constexpr bool TR_OUT = std::is_same<R, float>::value && MC == 512 && RAD == 8 && S == 1;
+    constexpr bool TR_IN = std::is_same<R, float>::value && MC == 512 && RAD == 8 && S == 8;
     const int line = (int)threadIdx.x / TPL, lt = (int)threadIdx.x % TPL;
     const bool act = line < nlines;
     cx<R> a[NB][RAD];
     if (act) {
 #pragma unroll
       for (int i = 0; i < NB; i++) {
-        const cx<R>* x = buf + line * ldm + pad(lt + i * TPL);
+        if constexpr (TR_IN) {
+          const int j = lt + i * TPL;
+          const cx<R>* x = buf + line * ldm + 66 * (j & 7) + (j >> 3);
 #pragma unroll
-        for (int u = 0; u < RAD; u++) a[i][u] = x[u * nbl + ((u * nbl) >> 5)];
+          for (int u = 0; u < RAD; u++) a[i][u] = x[8 * u + ((8 * u) >> 5)];
+        } else {
+          const cx<R>* x = buf + line * ldm + pad(lt + i * TPL);
+#pragma unroll
+          for (int u = 0; u < RAD; u++) a[i][u] = x[u * nbl + ((u * nbl) >> 5)];
+        }
       }
     }
     team_sync<TPL>();
@@ -337,6 +354,15 @@ __device__ __forceinline__ void fft_stage_ct(cx<R>* buf, int nlines, int ldm, co
         const int j = lt + i * TPL;
         const int p = j / S, q = j % S;
         dft_r<R, RAD, INV>(a[i]);
+        if constexpr (TR_OUT) {
+          // output 8p + t at pad(64t + p) = pad(p) + 66t (p < 64)
+          cx<R>* y = buf + line * ldm + pad(p);
+          const cx<R>* w = tw + TWOFF + p * (RAD - 1);
+          y[0] = a[i][0];
+#pragma unroll
+          for (int t = 1; t < RAD; t++) y[66 * t] = INV ? cmulc(a[i][t], w[t - 1]) : cmul(a[i][t], w[t - 1]);
+          continue;
+        }
         cx<R>* y = buf + line * ldm + pad(q + S * RAD * p);
         y[0] = a[i][0];
         if constexpr (S * RAD == MC) {
