@@ -57,12 +57,13 @@ def replica_aggregate(ms_local: float, points_local: int, dist=None, device="cpu
     return ms, p.item() / (ms * 1e-3) / 1e9
 
 
-# device-code sources of the solve pipeline (host-side plan code is not part of the hash)
+# device-code sources of the solve pipeline's kernels (host-side plan code, and the refinement and
+# face kernels of pp_misc.cu, which the profiled FP64 solve does not launch, are not part of the hash)
 KERNEL_SOURCES = ("pp_arith.cuh", "pp_fft.cuh", "pp_internal.h", "pp_lines.cuh", "pp_lines.cu", "pp_lines_df_tiny.cu",
                   "pp_lines_f32_tiny.cu", "pp_lines_df_small.cu",
                   "pp_lines_df_large.cu", "pp_lines_df_any.cu", "pp_lines_df_any57.cu", "pp_lines_f32_small.cu",
                   "pp_lines_f32_large.cu", "pp_lines_f32_any.cu", "pp_lines_f32_any57.cu", "pp_lines_df_ct3a.cu",
-                  "pp_lines_df_ct3b.cu", "pp_lines_f32_ct3a.cu", "pp_lines_f32_ct3b.cu", "pp_zsolve.cu", "pp_zpart.cu", "pp_misc.cu",
+                  "pp_lines_df_ct3b.cu", "pp_lines_f32_ct3a.cu", "pp_lines_f32_ct3b.cu", "pp_zsolve.cu", "pp_zpart.cu",
                   "pp_zfft.cu", "pp_range.cuh", "pp_zmul.cuh")
 
 

@@ -27,13 +27,39 @@ def test_mixed_error_bound(oracle, bc, dtype):
 
 
 @pytest.mark.parametrize("bc", ["PPPPPP", "NNNNNN", "NNDDNN"])
-def test_refined_recovers_fp64(oracle, bc):
+@pytest.mark.parametrize("sp", [(1.0 / 96, 1.0 / 48, 1.0 / 24), (0.01, 0.01, 0.01)])
+def test_refined_recovers_fp64(oracle, bc, sp):
+    """Unequal spacings scale each axis's second difference; equal ones scale their sum once."""
     shape = (24, 48, 96)
-    sp = (1.0 / 96, 1.0 / 48, 1.0 / 24)
     f = workloads.uniform_source(shape, seed=3)
     ref = oracle.solve(f, bc, sp)
     u = gpu_solve(f, bc, sp, "mixed_f64io", how="solve_refined")
     assert rel_l2(u, ref) <= 1e-10, rel_l2(u, ref)
+
+
+@pytest.mark.parametrize("bc", ["NNDDNN", "NNNNNN", "PPPPPP", "DNNDPP"])
+@pytest.mark.parametrize("spacing", [(1.0 / 20, 1.0 / 12, 1.0 / 10), (0.1, 0.1, 0.1)])
+def test_refined_alignment_paths(bc, spacing):
+    """The residual r = f - A u0 runs four cells a thread when nx is a multiple of 4 and f is 16-byte
+    aligned, the update u = u0 + delta four values a thread when u is; otherwise one a thread.  Both
+    forms do the same operations on the same operands, so a source or an output that starts 8 bytes
+    past a 16-byte boundary (and a row length that is not a multiple of 4) gives the same bits."""
+    import paper_1909_05423_gb300 as pp
+    for shape in ((10, 12, 20), (6, 10, 14)):
+        plan = pp.Plan(shape, bc, spacing, "mixed_f64io")
+        h = workloads.uniform_source(shape, seed=31)
+        f = torch.from_numpy(h).cuda()
+        u_al = plan.solve_refined(f)
+        fbuf = torch.empty((f.numel() + 1,), dtype=torch.float64, device="cuda")
+        f_off = fbuf[1:].view(shape)
+        f_off.copy_(f)
+        ubuf = torch.full((f.numel() + 1,), float("nan"), dtype=torch.float64, device="cuda")
+        u_off = ubuf[1:].view(shape)
+        assert f_off.data_ptr() % 16 == 8 and u_off.data_ptr() % 16 == 8
+        plan.solve_refined(f_off, u_off)
+        torch.cuda.synchronize()
+        assert torch.equal(u_al, u_off), shape
+        plan.close()
 
 
 @pytest.mark.parametrize("bc", ["PPPPDD", "NNDDNN", "DNPPNN", "PPPPPP", "NNNNNN"])
