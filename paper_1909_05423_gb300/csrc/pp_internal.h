@@ -185,9 +185,10 @@ struct pp_plan {
   int threads_z, lpc_z, ldm_z;
   // non-periodic z: 1 = Thomas sweeps, M = partitioned solve with M rows per chunk
   int zsplit;
-  // created with autotune = 1 (launch shapes timed), and whether the autotuner also chose zsplit;
-  // a batched graph may swap these members to the library's shared-GPU settings (pp_solve_batched)
-  bool tuned, zsplit_tuned;
+  // created with autotune = 1 (launch shapes timed), and whether the autotuner also chose the z
+  // algorithm (zsplit for non-periodic z, zmethod for periodic z); a batched graph may swap these
+  // members to the library's shared-GPU settings (pp_solve_batched)
+  bool tuned, z_tuned;
 };
 
 namespace pp {

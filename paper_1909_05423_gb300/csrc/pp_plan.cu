@@ -1036,9 +1036,9 @@ void evict_plan(const pp_plan* p) {
 }
 }  // namespace
 
-// Launch settings of a plan that a batched graph may swap: launch shapes and the z split.
+// Launch settings of a plan that a batched graph may swap: launch shapes and the z algorithm.
 struct PlanSettings {
-  int threads_x[2], lpc_x[2], ldm_x, threads_y[2], lpc_y[2], ldm_y, threads_z, lpc_z, ldm_z, zsplit;
+  int threads_x[2], lpc_x[2], ldm_x, threads_y[2], lpc_y[2], ldm_y, threads_z, lpc_z, ldm_z, zsplit, zmethod;
 };
 static PlanSettings get_settings(const pp_plan* p) {
   PlanSettings s;
@@ -1049,6 +1049,7 @@ static PlanSettings get_settings(const pp_plan* p) {
   s.ldm_x = p->ldm_x; s.ldm_y = p->ldm_y;
   s.threads_z = p->threads_z; s.lpc_z = p->lpc_z; s.ldm_z = p->ldm_z;
   s.zsplit = p->zsplit;
+  s.zmethod = p->zmethod;
   return s;
 }
 static void set_settings(pp_plan* p, const PlanSettings& s) {
@@ -1059,12 +1060,14 @@ static void set_settings(pp_plan* p, const PlanSettings& s) {
   p->ldm_x = s.ldm_x; p->ldm_y = s.ldm_y;
   p->threads_z = s.threads_z; p->lpc_z = s.lpc_z; p->ldm_z = s.ldm_z;
   p->zsplit = s.zsplit;
+  p->zmethod = s.zmethod;
 }
 
 // Puts the autotuned members of a batch on the library's shared-GPU settings -- the default launch
-// shapes and, where the autotuner chose the z split, the Thomas sweeps -- for the scope of one
-// capture, and restores their own settings afterwards (a captured graph keeps the launch
-// parameters it was captured with).
+// shapes and, where the autotuner chose the z algorithm, the Thomas or Sherman-Morrison sweeps
+// (the partitioned solve and the z transform buy a lone plan latency with extra work) -- for the
+// scope of one capture, and restores their own settings afterwards (a captured graph keeps the
+// launch parameters it was captured with).
 struct SettingsSwap {
   std::vector<std::pair<pp_plan*, PlanSettings>> saved;
   void apply(pp_plan* const* plans, int n) {
@@ -1076,7 +1079,10 @@ struct SettingsSwap {
       if (seen) continue;
       saved.emplace_back(p, get_settings(p));
       choose_shapes(p, nullptr);
-      if (p->zsplit_tuned) p->zsplit = 1;
+      if (p->z_tuned) {
+        p->zsplit = 1;
+        p->zmethod = ZM_SM;
+      }
     }
   }
   ~SettingsSwap() {
@@ -1312,7 +1318,7 @@ pp_status pp_plan_create(pp_plan** out, int nx, int ny, int nz, const pp_bc bc[6
     pp_status ts = autotune(p, zreq == 0, sreq == 0 && !zper);
     if (ts != PP_OK) { free_plan(p); return ts; }
     p->tuned = true;
-    p->zsplit_tuned = (sreq == 0 && !zper);
+    p->z_tuned = zper ? (zreq == 0 && zfft_ok) : (sreq == 0);
   }
   *out = p;
   return PP_OK;
