@@ -64,6 +64,21 @@ __device__ __forceinline__ void zload(S* v, const S* base, long long P, int k0, 
     if (k >= 0 && k < n) v[u] = base[(long long)k * P];
   }
 }
+// The same for a batch that lies wholly in [0, n), from q = base + k0 P: no tests, and each address
+// one 32 x 32 -> 64-bit multiply-add of the plane stride (P32 = P < 2^31 for every plan) instead of
+// a 64-bit product (the FP32-spill sweeps are bound by instruction issue).
+template <int ZU, class S>
+__device__ __forceinline__ void zload_full(S* v, const S* q, int P32, int step) {
+#pragma unroll
+  for (int u = 0; u < ZU; u++) v[u] = q[(long long)(step * u) * P32];
+}
+// batch loads of the sweeps: unchecked where the whole batch lies in [0, n)
+template <int ZU, class S>
+__device__ __forceinline__ void zload_batch(S* v, const S* base, long long P, int P32, int k0, int step, int n) {
+  const int klast = k0 + step * (ZU - 1);
+  if (k0 >= 0 && k0 < n && klast >= 0 && klast < n) zload_full<ZU>(v, base + (long long)k0 * P, P32, step);
+  else zload<ZU>(v, base, P, k0, step, n);
+}
 
 // The singular mode: remove the source mean, pin u_0 = 0, solve rows 1..n-1, shift to zero mean.
 template <class S>
@@ -169,16 +184,18 @@ __device__ __forceinline__ void z_sweeps(const ZArgs& a, const ZMode& m, S* base
     // forward elimination g_k = (s d_k - g_{k-1}) w_k; periodic: y0 = sum q_k s d_k
     df g = df{0.f, 0.f};
     df y0 = df{0.f, 0.f};
-    zload<ZU>(cur, base, P, 0, 1, n);
+    const int P32 = (int)P;
+    zload_batch<ZU>(cur, base, P, P32, 0, 1, n);
     for (int k0 = 0; k0 < n; k0 += ZU) {
-      if (k0 + ZU < n) zload<ZU>(nxt, base, P, k0 + ZU, 1, n);
+      if (k0 + ZU < n) zload_batch<ZU>(nxt, base, P, P32, k0 + ZU, 1, n);
       if (ZFast<S, MODE>::v && k0 >= wlen && k0 >= qlen && k0 + ZU < n) {
+        S* const q = base + (long long)k0 * P;
 #pragma unroll
         for (int u = 0; u < ZU; u++) {
           const df d = zscaled(cur[u], scale);
           track(dmax, d.hi);
           g = zr_fwd<S, N1>(d, g, winf);
-          zput(base + (k0 + u) * P, g);
+          zput(q + (long long)u * P32, g);
         }
       } else {
 #pragma unroll
@@ -203,15 +220,16 @@ __device__ __forceinline__ void z_sweeps(const ZArgs& a, const ZMode& m, S* base
       cg = c * f2df(m.gam);
     }
     df u = df{0.f, 0.f};
-    zload<ZU>(cur, base, P, n - 1, -1, n);
+    zload_batch<ZU>(cur, base, P, P32, n - 1, -1, n);
     for (int k0 = n - 1; k0 >= 0; k0 -= ZU) {
-      if (k0 - ZU >= 0) zload<ZU>(nxt, base, P, k0 - ZU, -1, n);
+      if (k0 - ZU >= 0) zload_batch<ZU>(nxt, base, P, P32, k0 - ZU, -1, n);
       if (ZFast<S, MODE>::v && k0 - ZU + 1 >= wlen && k0 - ZU + 1 >= qlen && k0 < n - 1) {
+        S* const q = base + (long long)k0 * P;
 #pragma unroll
         for (int t = 0; t < ZU; t++) {
           u = zr_bwd<S, N1>(zcvt(cur[t]), winf, u);
           track(umax, u.hi);
-          zput(base + (k0 - t) * P, u);
+          zput(q - (long long)t * P32, u);
         }
 #pragma unroll
         for (int t = 0; t < ZU; t++) cur[t] = nxt[t];
@@ -237,9 +255,10 @@ __device__ __forceinline__ void z_sweeps(const ZArgs& a, const ZMode& m, S* base
     // transposed factorisation T^T = U^T L^T:  h_k = s d_k - w_{k-1} h_{k-1},  x_k = (h_k - x_{k+1}) w_k
     df h = df{0.f, 0.f};
     df wprev = df{0.f, 0.f};
-    zload<ZU>(cur, base, P, 0, 1, n);
+    const int P32 = (int)P;
+    zload_batch<ZU>(cur, base, P, P32, 0, 1, n);
     for (int k0 = 0; k0 < n; k0 += ZU) {
-      if (k0 + ZU < n) zload<ZU>(nxt, base, P, k0 + ZU, 1, n);
+      if (k0 + ZU < n) zload_batch<ZU>(nxt, base, P, P32, k0 + ZU, 1, n);
 #pragma unroll
       for (int u = 0; u < ZU; u++) {
         const int k = k0 + u;
@@ -255,9 +274,9 @@ __device__ __forceinline__ void z_sweeps(const ZArgs& a, const ZMode& m, S* base
       for (int u = 0; u < ZU; u++) cur[u] = nxt[u];
     }
     df x = df{0.f, 0.f};
-    zload<ZU>(cur, base, P, n - 1, -1, n);
+    zload_batch<ZU>(cur, base, P, P32, n - 1, -1, n);
     for (int k0 = n - 1; k0 >= 0; k0 -= ZU) {
-      if (k0 - ZU >= 0) zload<ZU>(nxt, base, P, k0 - ZU, -1, n);
+      if (k0 - ZU >= 0) zload_batch<ZU>(nxt, base, P, P32, k0 - ZU, -1, n);
 #pragma unroll
       for (int t = 0; t < ZU; t++) {
         const int k = k0 - t;
