@@ -186,10 +186,11 @@ pp_status pp_fold_bc(pp_plan* plan, const void* f_in, void* f_out, const void* c
  * waits for `stream` to be idle, allocates scratch grids of the members' sizes for the duration
  * of the call, and times the graph with the members' own settings and with the default launch
  * shapes and z sweeps (Thomas; Sherman-Morrison for periodic z) for the autotuned members; the
- * faster is kept for that list of plans
- * (the plans themselves keep their settings for pp_solve).  Without the scratch memory the
- * members' own settings are used.  Errors: PP_ERR_INVALID_ARG (n < 0, NULL arrays or members),
- * PP_ERR_CUDA (capture/instantiate/launch). */
+ * faster is kept for that list of plans (the plans themselves keep their settings for pp_solve).
+ * Without the scratch memory, or while `stream` is being captured into a graph, the members' own
+ * settings are used.
+ * Errors: PP_ERR_INVALID_ARG (n < 0, NULL arrays or members), PP_ERR_CUDA (capture/instantiate/
+ * launch). */
 pp_status pp_solve_batched(pp_plan* const* plans, const void* const* f, void* const* u, int n,
                            pp_stream_t stream);
 

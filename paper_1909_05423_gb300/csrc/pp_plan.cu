@@ -1410,6 +1410,12 @@ pp_status pp_solve_batched(pp_plan* const* plans, const void* const* f, void* co
   int choice = 0;
   bool any_tuned = false;
   for (int i = 0; i < n; i++) any_tuned |= plans[i]->tuned;
+  // No tuning while the caller's stream is being captured: it waits for the stream and launches
+  // timing runs, neither of which belongs in the caller's graph (the members keep their settings,
+  // and a later call outside a capture tunes the list).
+  cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+  if (any_tuned && (cudaStreamIsCapturing(st, &cap_status) != cudaSuccess || cap_status != cudaStreamCaptureStatusNone))
+    any_tuned = false;
   if (any_tuned) {
     const std::vector<const pp_plan*> pk(plans, plans + n);
     bool found = false;
